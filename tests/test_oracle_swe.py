@@ -1,0 +1,87 @@
+"""Pins of the oracle F(u) and J(u)x.
+
+* F is quadratic in u, so the central difference (F(u+e x) - F(u-e x))/(2e) is
+  exactly J(u)x up to rounding for any e: this pins every term of the Jacobian
+  blocks of Eqs. (eq:dynja)-(eq:dynjc) against F of Eq. (eq:sweqsinv), and in
+  particular the reading of the second row of J_r (the printed signs fail).
+* Mass: sum_i A_i (dh/dt)_i = 0 for every state (flux form), and a^T J = 0 for
+  the mass functional a.
+* A fluid at rest with flat height is a steady state: F = 0.
+* Quadratic structure: F(u+d) - F(u) - J(u)d does not depend on u; it is the
+  quadratic part Q(d) = F(d) - J(0)d (used for D_ni and R_{n-1}).
+"""
+import numpy as np
+import pytest
+
+from paper_1805_02144_gb300.inputs import balanced_state, random_vector
+
+from conftest import oracle_swe
+
+
+@pytest.mark.parametrize("lev,seed", [(2, 1), (3, 2), (4, 3)])
+def test_jv_equals_central_difference(lev, seed):
+    s = oracle_swe(lev)
+    u = balanced_state(s.grid.x, seed, 400.0)
+    for k in range(3):
+        x = random_vector(s.n, 100 + k) * np.concatenate([np.full(3 * s.ng, 10.0), np.full(s.ng, 100.0)])
+        jx = s.Jv(u, x)
+        eps = 1.0
+        fd = (s.F(u + eps * x) - s.F(u - eps * x)) / (2 * eps)
+        assert np.linalg.norm(fd - jx) <= 1e-12 * np.linalg.norm(jx)
+
+
+def test_printed_jr_row2_signs_fail_the_difference_check():
+    """Planting the printed signs [eta n_z, ., -eta n_x] in J_r row 2 breaks J = dF/du."""
+    s = oracle_swe(3)
+    u = balanced_state(s.grid.x, 1, 200.0)
+    x = random_vector(s.n, 5)
+    ng = s.ng
+    n = s.grid.x
+    eta = s.vorticity(*s.split(u)[:3]) + s.f
+    xx, xy, xz, _ = s.split(x)
+    printed = s.Jv(u, x).copy()
+    printed[ng:2 * ng] += 2.0 * eta * (n[:, 2] * xx - n[:, 0] * xz)
+    fd = (s.F(u + x) - s.F(u - x)) / 2.0
+    assert np.linalg.norm(fd - printed) > 1e-6 * np.linalg.norm(fd)
+
+
+def test_assembled_jacobian_matches_matrix_free():
+    s = oracle_swe(2)
+    u = balanced_state(s.grid.x, 3, 300.0)
+    J = s.jacobian(u)
+    x = random_vector(s.n, 9)
+    assert np.linalg.norm(J @ x - s.Jv(u, x)) <= 1e-14 * np.linalg.norm(J @ x)
+
+
+def test_mass_is_conserved_by_F_and_J():
+    s = oracle_swe(4)
+    u = balanced_state(s.grid.x, 2, 400.0)
+    a = s.grid.area
+    Fh = s.split(s.F(u))[3]
+    assert abs(np.sum(a * Fh)) <= 1e-13 * np.sum(a * np.abs(Fh))
+    x = random_vector(s.n, 4)
+    Jh = s.split(s.Jv(u, x))[3]
+    assert abs(np.sum(a * Jh)) <= 1e-13 * np.sum(a * np.abs(Jh))
+
+
+def test_rest_state_is_steady():
+    s = oracle_swe(3)
+    u = np.concatenate([np.zeros(3 * s.ng), np.full(s.ng, 5960.0)])
+    F = s.F(u)
+    # momentum: -G(g h) of a constant; continuity: -D(0); both vanish
+    assert np.max(np.abs(F)) < 1e-12 * s.g * 5960.0 / s.grid.radius
+
+
+def test_quadratic_remainder_is_independent_of_base_state():
+    s = oracle_swe(3)
+    u1 = balanced_state(s.grid.x, 1, 200.0)
+    u2 = balanced_state(s.grid.x, 7, 400.0)
+    d = balanced_state(s.grid.x, 11, 50.0)
+    d[3 * s.ng:] -= 5960.0
+    r1 = s.F(u1 + d) - s.F(u1) - s.Jv(u1, d)
+    r2 = s.F(u2 + d) - s.F(u2) - s.Jv(u2, d)
+    q = s.F(d) - s.Jv(np.zeros(s.n), d)
+    scale = np.linalg.norm(s.F(u1))
+    assert np.linalg.norm(r1 - q) <= 1e-12 * scale
+    assert np.linalg.norm(r2 - q) <= 1e-12 * scale
+    assert np.linalg.norm(q) > 1e-8 * scale
