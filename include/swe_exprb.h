@@ -1,0 +1,206 @@
+/*
+ * swe_exprb.h -- C ABI of the GB300 exponential Rosenbrock shallow-water path.
+ *
+ * Method: Luan, Pudykiewicz, Reynolds, "Further development of efficient and
+ * accurate time integration schemes for meteorological models"
+ * (arXiv:1805.02144).  Equation names below are the paper's LaTeX labels
+ * (eq3.17 etc.), because its printed numbering restarts in every section.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * State layout (Sec. 2, Eq. eq:dynu): u = (u_x, u_y, u_z, h), four planes of
+ *   ncells doubles each, n = 4*ncells, cells in the grid's own order (a
+ *   space-filling-curve order; swe_grid_cell_centres gives each cell's
+ *   position so callers can build inputs in that order).
+ * Pointers: every double* / const double* vector argument is a DEVICE pointer
+ *   to n contiguous float64 values, owned by the caller; the library never
+ *   frees or retains it beyond the call's stream work.  Arguments documented
+ *   as "host" are plain host memory read during the call.
+ * Streams: work is enqueued on `stream` (a cudaStream_t passed as void*,
+ *   NULL = legacy default stream) and returns before it completes, except
+ *   where a host result is requested (phi_stats), which waits for the stream.
+ * Errors: every int-returning call returns SWE_OK (0) or a negative SWE_ERR_*
+ *   code; swe_last_error() gives a message for the calling thread.  Errors
+ *   found on the device (no convergence, non-finite values, a wait that ran
+ *   out) are reported in phi_stats.status and by swe_device_status().
+ * Grid handles are not thread-safe: one host thread per grid at a time.
+ */
+#ifndef SWE_EXPRB_H
+#define SWE_EXPRB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  SWE_OK = 0,
+  SWE_ERR_INVALID_ARG = -1,
+  SWE_ERR_NOMEM = -2,
+  SWE_ERR_NOCONV = -3,     /* substep controller gave up (Algorithm 1)        */
+  SWE_ERR_NONFINITE = -4,  /* NaN/Inf in a Krylov norm or coefficient          */
+  SWE_ERR_TIMEOUT = -5,    /* a bounded device-side wait expired               */
+  SWE_ERR_CUDA = -6
+};
+
+enum { SWE_EPI2 = 0, SWE_EXPRB42 = 1, SWE_PEXPRB43 = 2, SWE_EXPRB53 = 3, SWE_EPI3 = 4 };
+
+typedef struct swe_grid swe_grid; /* opaque, library-owned */
+
+/* Options of phipm_simul_iom2 (Sec. 4.3, Algorithm 1 and its initialisation).
+ * Call swe_phi_opts_default() and change fields. */
+typedef struct {
+  double tol;        /* Tol of Algorithm 1 step 6                                  */
+  int tol_mode;      /* 0: relative, Tol scaled by max_l ||v_l||_2; 1: absolute     */
+  int m_init;        /* initial Krylov size (Algorithm 1: 1)                       */
+  int m_max;         /* largest Krylov size, <= 64                                 */
+  int iom;           /* orthogonalisation window, must be 2 (IOM2)                 */
+  double delta;      /* acceptance safety factor (Algorithm 1: 1.4)                */
+  double gamma;      /* controller target for omega (0.8)                          */
+  double kappa;      /* assumed error decrease per Krylov dimension (2)            */
+  int max_reject;    /* SWE_ERR_NOCONV after this many rejections in one call      */
+  int m_carry;       /* exprb_step: start each call slot at its last accepted m    */
+  const double* replay;  /* host, optional: 3 doubles (tau, m, accepted) per attempt;
+                            when non-NULL the step sizes, Krylov sizes and decisions
+                            are taken from it instead of the controller            */
+  int n_replay;      /* number of attempts in replay                               */
+} phi_opts;
+
+/* One controller attempt (trace record). */
+typedef struct {
+  double t, tau, omega;
+  int m, accepted, call;  /* call: index of the phi evaluation within exprb_step */
+  int pad;
+} phi_attempt;
+
+typedef struct {
+  int n_jv;          /* Jacobian-vector products                 */
+  int n_substeps;    /* accepted substeps                        */
+  int n_reject;      /* rejected attempts                        */
+  int m_last;        /* Krylov size of the last accepted substep */
+  int m_max_used;
+  int status;        /* SWE_OK or a negative SWE_ERR_* found on the device */
+  phi_attempt* trace;  /* host buffer provided by the caller, or NULL */
+  int trace_cap;       /* capacity of trace                          */
+  int n_trace;         /* attempts written (<= trace_cap)            */
+} phi_stats;
+
+void swe_phi_opts_default(phi_opts* opts);
+
+/* Build the level-`level` icosahedral geodesic Voronoi grid (Sec. 2: N_g =
+ * 10*4^level + 2 cells, Voronoi control volumes, finite-volume operators
+ * G, D, V, L of Eqs. eq:sweqsinv, eq:vort, eq:swdis) on the host, reorder it
+ * along a space-filling curve when `reorder` != 0, and upload the operator
+ * tables to the current CUDA device.  radius a [m], g [m s^-2], omega [s^-1],
+ * gamma_h of Eq. eq:niu.  0 <= level <= 10.  The handle owns all device
+ * memory it allocates (tables and the phi_action / exprb_step workspace). */
+int swe_create_grid(int level, double radius, double g, double omega, double gamma_h,
+                    int reorder, swe_grid** out);
+void swe_destroy_grid(swe_grid* grid);
+
+/* The same grid built on the host only (no CUDA call, no device memory):
+ * queries and swe_grid_export work, compute entry points return
+ * SWE_ERR_INVALID_ARG.  For preparing inputs or checking tables on a machine
+ * without a GPU. */
+int swe_create_grid_host(int level, double radius, double g, double omega, double gamma_h,
+                         int reorder, swe_grid** out);
+
+/* Host copy of one operator table, in the grid's cell order; `count` must be
+ * the table's element count (error otherwise).  Names and layouts
+ * (ncells = N_g, slot k = 0..5, component c = 0..2):
+ *   "nbr"  int32  [6][N_g] neighbour of slot k (pentagons: slot 5 = the cell)
+ *   "wl"   double [6][N_g] l_e/(d_e A_i);  "wld" double [N_g] -sum_k wl
+ *   "nc"   double [3][6][N_g] edge-value weight x l_e nu_e/A_i of slot k
+ *   "ndd"  double [3][N_g]    the same for the cell itself (D diagonal)
+ *   "sdg"  double [3][N_g]    sum_e l_e nu_e / A_i (G diagonal = ndd - sdg)
+ *   "vc", "vd" double: as nc, ndd with the edge tangent t_e
+ * so that (L psi)_i = wld psi_i + sum_k wl psi_nbr, (D.q)_i = ndd.q_i +
+ * sum_k nc.q_nbr, (V.u)_i = vd.u_i + sum_k vc.u_nbr and
+ * (G psi)_i = P_i[(ndd - sdg) psi_i + sum_k nc psi_nbr]. */
+int swe_grid_export(const swe_grid* grid, const char* table, void* host_out, int64_t count);
+
+/* Sizes and constants: ncells, n = 4*ncells, n_A = structural nonzeros of J
+ * (the n_A of the cost function Eq. eq:cost), nu of Eq. eq:niu.  Any output
+ * pointer may be NULL. */
+int swe_grid_query(const swe_grid* grid, int64_t* ncells, int64_t* n, int64_t* nA, double* nu);
+
+/* Host output: unit cell centres, 3*ncells doubles laid out x[ncells],
+ * y[ncells], z[ncells], in the grid's cell order. */
+int swe_grid_cell_centres(const swe_grid* grid, double* xyz_host);
+
+/* Host output: cell areas A_i [m^2] (ncells doubles), grid order. */
+int swe_grid_cell_areas(const swe_grid* grid, double* area_host);
+
+/* f = F(u), the semi-discrete shallow-water right-hand side of Eq. eq:sweqsinv
+ * with the dissipation -nu L^2 of Eq. eq:swdis on every variable.  u, f:
+ * device, n doubles, must not overlap. */
+int swe_rhs(const swe_grid* grid, const double* u, double* f, void* stream);
+
+/* jx = J(u) x, the Jacobian J = J_v + J_r + J_m of Eqs. eq:dynja-eq:dynjc
+ * (second row of J_r taken as the derivative of F, see the oracle).  u, x, jx:
+ * device, n doubles; jx must not overlap u or x. */
+int swe_jv(const swe_grid* grid, const double* u, const double* x, double* jx, void* stream);
+
+/* phipm_simul_iom2 (Sec. 4.3, Algorithm 1): for A = dt*J(u_lin) and vectors
+ * v_0..v_p, writes y_out[i] = sum_{l=0}^{p} rho_i^l phi_l(rho_i A) v_l
+ * (Eq. eq:exp_multistage with the rho^l factor the drivers of Sec. 4.4 use),
+ * i = 0..ns-1, by adaptive substepping (Eqs. eq3.17-eq3.18) with IOM2 Krylov
+ * projections, all on the device in one persistent launch.
+ *   v: host array of p+1 device pointers; a NULL entry is a zero vector.
+ *   rho: host array, 0 < rho_0 < ... < rho_{ns-1} <= 1.  1 <= p <= 4, 1 <= ns <= 8.
+ *   y_out: host array of ns device pointers (distinct from u_lin and v).
+ *   opts: NULL = defaults.  stats: NULL, or filled after waiting for the stream.
+ * The first call on a grid allocates its workspace (outside any stream capture). */
+int phi_action(swe_grid* grid, const double* u_lin, double dt, int p,
+               const double* const* v, int ns, const double* rho,
+               double* const* y_out, const phi_opts* opts, phi_stats* stats, void* stream);
+
+/* Per-scheme history (epi3's previous state, the m carried per call slot).
+ * Create one per trajectory; reset before a new trajectory. */
+typedef struct swe_scheme_state swe_scheme_state;
+int swe_scheme_state_create(const swe_grid* grid, swe_scheme_state** out);
+int swe_scheme_state_reset(swe_scheme_state* st);
+void swe_scheme_state_destroy(swe_scheme_state* st);
+
+/* One step u_{n+1} of EPI2 (Eq. eq3.5), exprb42 (eq3.11), pexprb43 (eq3.12),
+ * exprb53 (eq3.13) or epi3 (eq_epi3, which starts with one EPI2 step), with
+ * the phipm_simul_iom2 calls of Sec. 4.4.  u_n, u_np1: device, n doubles,
+ * distinct.  state: required (epi3 history, m carry).  stats accumulate over
+ * the step's phi calls. */
+int exprb_step(swe_grid* grid, int scheme, double dt, const double* u_n, double* u_np1,
+               swe_scheme_state* state, const phi_opts* opts, phi_stats* stats, void* stream);
+
+/* Opt-in timing and operation counts (CUDA events recorded on the call's
+ * stream around every persistent phi launch and every exprb_step / phi_action
+ * call; counters of IOM2 iterations, w_j products and combination terms kept
+ * on the device).  phi_flop is the FP64 operation count of the phi launches
+ * (per cell: 342 per IOM2 iteration, 310 per w_j product, 8 per combination
+ * term); phi_bytes the algorithmic vector bytes (per cell: 136 per IOM2
+ * iteration, 104 per w_j product, 32 per combination term), operator tables
+ * excluded. */
+typedef struct {
+  double phi_ms;          /* summed duration of the persistent phi launches  */
+  double call_ms;         /* summed duration of the whole calls              */
+  double phi_flop;
+  double phi_bytes;
+  int64_t phi_launches;   /* persistent phi launches                         */
+  int64_t kernel_launches;/* all kernels launched by the calls (phi included) */
+  int64_t iom2_iterations, w_jv, comb_terms;
+} swe_profile;
+
+/* on != 0: zero the counters and start recording; on == 0: stop. */
+int swe_profile_enable(swe_grid* grid, int on);
+/* Waits for `stream`, then fills *out with the totals since enabling. */
+int swe_profile_read(swe_grid* grid, swe_profile* out, void* stream);
+
+/* Waits for `stream` and returns the first device-side error of the grid's
+ * last phi_action / exprb_step (SWE_OK if none), clearing it. */
+int swe_device_status(swe_grid* grid, void* stream);
+
+const char* swe_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SWE_EXPRB_H */

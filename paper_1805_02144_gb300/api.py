@@ -1,0 +1,217 @@
+"""Python surface over the C ABI, with the same names (torch tensors in, out).
+
+Vectors are torch float64 CUDA tensors of n = 4 * ncells elements in the
+grid's cell order; work is enqueued on the current torch CUDA stream unless a
+stream is given.  Nothing here computes: each function checks arguments,
+passes device pointers to libswe_exprb.so and raises on a nonzero status.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from typing import Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import PhiAttemptC, PhiStatsC, SCHEMES, check, default_opts, load
+
+EARTH_RADIUS = 6.37122e6
+GRAVITY = 9.80616
+OMEGA = 7.292e-5
+GAMMA_H = 0.04e-2
+
+
+def _stream(stream) -> C.c_void_p:
+    if stream is None:
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, torch.cuda.Stream):
+        return C.c_void_p(stream.cuda_stream)
+    return C.c_void_p(int(stream))
+
+
+def _ptr(t: Optional[torch.Tensor], n: int, name: str) -> C.c_void_p:
+    if t is None:
+        return C.c_void_p(0)
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64:
+        raise TypeError(f"{name} must be a CUDA float64 tensor")
+    if not t.is_contiguous() or t.numel() != n:
+        raise ValueError(f"{name} must be contiguous with {n} elements")
+    return C.c_void_p(t.data_ptr())
+
+
+class Grid:
+    """Handle of swe_create_grid (icosahedral geodesic grid + operator tables)."""
+
+    def __init__(self, level: int, radius: float = EARTH_RADIUS, g: float = GRAVITY,
+                 omega: float = OMEGA, gamma_h: float = GAMMA_H, reorder: bool = True,
+                 host_only: bool = False):
+        L = load()
+        h = C.c_void_p()
+        create = L.swe_create_grid_host if host_only else L.swe_create_grid
+        check(create(level, radius, g, omega, gamma_h, int(reorder), C.byref(h)))
+        self.handle = h
+        self.level = level
+        nc, n, nA, nu = C.c_int64(), C.c_int64(), C.c_int64(), C.c_double()
+        check(L.swe_grid_query(h, C.byref(nc), C.byref(n), C.byref(nA), C.byref(nu)))
+        self.ncells, self.n, self.nA, self.nu = nc.value, n.value, nA.value, nu.value
+
+    def cell_centres(self) -> np.ndarray:
+        out = np.empty(3 * self.ncells)
+        check(load().swe_grid_cell_centres(self.handle, out.ctypes.data_as(C.POINTER(C.c_double))))
+        return out.reshape(3, self.ncells).T.copy()
+
+    def cell_areas(self) -> np.ndarray:
+        out = np.empty(self.ncells)
+        check(load().swe_grid_cell_areas(self.handle, out.ctypes.data_as(C.POINTER(C.c_double))))
+        return out
+
+    def export(self, table: str) -> np.ndarray:
+        """Host copy of an operator table (see swe_grid_export), shaped [..., ncells]."""
+        ng = self.ncells
+        shapes = {"nbr": (6, ng), "wl": (6, ng), "wld": (ng,), "nc": (3, 6, ng), "ndd": (3, ng),
+                  "sdg": (3, ng), "vc": (3, 6, ng), "vd": (3, ng)}
+        out = np.empty(shapes[table], dtype=np.int32 if table == "nbr" else np.float64)
+        check(load().swe_grid_export(self.handle, table.encode(), out.ctypes.data_as(C.c_void_p),
+                                     out.size))
+        return out
+
+    def close(self) -> None:
+        if self.handle:
+            load().swe_destroy_grid(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def swe_create_grid(level: int, **kw) -> Grid:
+    return Grid(level, **kw)
+
+
+def _new(grid: Grid, like: Optional[torch.Tensor] = None) -> torch.Tensor:
+    dev = like.device if like is not None else torch.device("cuda")
+    return torch.empty(grid.n, dtype=torch.float64, device=dev)
+
+
+def swe_rhs(grid: Grid, u: torch.Tensor, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    out = _new(grid, u) if out is None else out
+    check(load().swe_rhs(grid.handle, _ptr(u, grid.n, "u"), _ptr(out, grid.n, "out"), _stream(stream)))
+    return out
+
+
+def swe_jv(grid: Grid, u: torch.Tensor, x: torch.Tensor, out: Optional[torch.Tensor] = None,
+           stream=None) -> torch.Tensor:
+    out = _new(grid, u) if out is None else out
+    check(load().swe_jv(grid.handle, _ptr(u, grid.n, "u"), _ptr(x, grid.n, "x"),
+                        _ptr(out, grid.n, "out"), _stream(stream)))
+    return out
+
+
+def _opts(opts) -> tuple[_lib.PhiOptsC, object]:
+    """Build a phi_opts struct from a dict; returns (struct, keep-alive)."""
+    if opts is None:
+        return default_opts(), None
+    if isinstance(opts, _lib.PhiOptsC):
+        return opts, None
+    o = default_opts(**{k: v for k, v in opts.items() if k != "replay"})
+    keep = None
+    if opts.get("replay") is not None:
+        rec = np.ascontiguousarray(np.asarray(opts["replay"], dtype=np.float64).reshape(-1, 3))
+        keep = rec
+        o.replay = rec.ctypes.data_as(C.POINTER(C.c_double))
+        o.n_replay = rec.shape[0]
+    return o, keep
+
+
+def _stats(trace_cap: int) -> tuple[PhiStatsC, object]:
+    st = PhiStatsC()
+    buf = None
+    if trace_cap > 0:
+        buf = (PhiAttemptC * trace_cap)()
+        st.trace = C.cast(buf, C.POINTER(PhiAttemptC))
+        st.trace_cap = trace_cap
+    return st, buf
+
+
+def _stats_dict(st: PhiStatsC) -> dict:
+    d = {k: getattr(st, k) for k in ("n_jv", "n_substeps", "n_reject", "m_last", "m_max_used", "status")}
+    d["trace"] = [dict(t=st.trace[i].t, tau=st.trace[i].tau, omega=st.trace[i].omega, m=st.trace[i].m,
+                       accepted=bool(st.trace[i].accepted), call=st.trace[i].call)
+                  for i in range(st.n_trace)]
+    return d
+
+
+def phi_action(grid: Grid, u_lin: torch.Tensor, dt: float, v: Sequence[Optional[torch.Tensor]],
+               rho: Sequence[float], out: Optional[Sequence[torch.Tensor]] = None, opts=None,
+               stats: bool = False, trace_cap: int = 0, stream=None):
+    """[sum_l rho_i^l phi_l(rho_i dt J(u_lin)) v_l for rho_i in rho] (Algorithm 1)."""
+    p = len(v) - 1
+    ns = len(rho)
+    outs = [_new(grid, u_lin) for _ in range(ns)] if out is None else list(out)
+    vp = (C.c_void_p * (p + 1))(*[_ptr(x, grid.n, f"v[{i}]") for i, x in enumerate(v)])
+    yp = (C.c_void_p * ns)(*[_ptr(y, grid.n, f"out[{i}]") for i, y in enumerate(outs)])
+    rh = (C.c_double * ns)(*[float(r) for r in rho])
+    o, keep = _opts(opts)
+    st, buf = _stats(trace_cap) if (stats or trace_cap) else (None, None)
+    check(load().phi_action(grid.handle, _ptr(u_lin, grid.n, "u_lin"), float(dt), p, vp, ns, rh, yp,
+                            C.byref(o), C.byref(st) if st is not None else None, _stream(stream)))
+    del keep, buf
+    return (outs, _stats_dict(st)) if st is not None else outs
+
+
+class SchemeState:
+    """swe_scheme_state: epi3 history and the Krylov size carried per call slot."""
+
+    def __init__(self, grid: Grid):
+        h = C.c_void_p()
+        check(load().swe_scheme_state_create(grid.handle, C.byref(h)))
+        self.handle = h
+        self.grid = grid
+
+    def reset(self) -> None:
+        check(load().swe_scheme_state_reset(self.handle))
+
+    def close(self) -> None:
+        if self.handle:
+            load().swe_scheme_state_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def exprb_step(grid: Grid, scheme: str, dt: float, u_n: torch.Tensor,
+               out: Optional[torch.Tensor] = None, state: Optional[SchemeState] = None, opts=None,
+               stats: bool = False, trace_cap: int = 0, stream=None):
+    """One step u_{n+1} of scheme in {epi2, exprb42, pexprb43, exprb53, epi3}."""
+    out = _new(grid, u_n) if out is None else out
+    if state is None:
+        raise ValueError("exprb_step needs a SchemeState (epi3 history, Krylov size carry)")
+    o, keep = _opts(opts)
+    st, buf = _stats(trace_cap) if (stats or trace_cap) else (None, None)
+    check(load().exprb_step(grid.handle, SCHEMES[scheme], float(dt), _ptr(u_n, grid.n, "u_n"),
+                            _ptr(out, grid.n, "out"), state.handle, C.byref(o),
+                            C.byref(st) if st is not None else None, _stream(stream)))
+    del keep, buf
+    return (out, _stats_dict(st)) if st is not None else out
+
+
+def swe_device_status(grid: Grid, stream=None) -> None:
+    check(load().swe_device_status(grid.handle, _stream(stream)))
+
+
+def swe_profile_enable(grid: Grid, on: bool = True) -> None:
+    check(load().swe_profile_enable(grid.handle, int(on)))
+
+
+def swe_profile_read(grid: Grid, stream=None) -> dict:
+    pr = _lib.ProfileC()
+    check(load().swe_profile_read(grid.handle, C.byref(pr), _stream(stream)))
+    return {k: getattr(pr, k) for k, _ in _lib.ProfileC._fields_}

@@ -1,0 +1,78 @@
+// Arguments and device control block of the persistent phipm_simul_iom2 launch.
+#pragma once
+#include <stdint.h>
+
+#include "swe_dev.cuh"
+
+namespace swe {
+
+constexpr int KMAX = 64;   // largest Krylov size
+constexpr int PMAX = 4;    // largest phi index p
+constexpr int NSMAX = 8;   // largest number of outputs rho_i
+constexpr int NRED = 8;    // values per grid reduction
+
+// Statistics accumulated on the device over one phi_action or one exprb_step.
+struct DevStats {
+  int n_jv, n_sub, n_rej, m_last, m_max_used, status, n_trace, pad;
+};
+
+// Operation counters accumulated while profiling is on.
+struct DevProfile {
+  long long iters, wjv, comb_terms, launches;
+};
+
+// One trace record, the same layout as the public phi_attempt.
+struct DevAttempt {
+  double t, tau, omega;
+  int m, accepted, call, pad;
+};
+
+// Control block written by one thread between grid barriers and read by all.
+struct PhiCtrl {
+  double red[NRED];
+  double hd[KMAX + 1];      // H[j][j]
+  double hu[KMAX + 1];      // H[j][j+1]
+  double hl[KMAX + 2];      // H[j][j-1]; hl[m] is h_{m+1,m} of an m-column basis
+  double sig[KMAX + 2];     // basis vector j = sig[j] * raw slot j
+  double cV[KMAX + 2];      // combination coefficients of raw slots 0..m
+  double cW[PMAX + 1];      // combination coefficients of w_0..w_{p-1}
+  double beta, scale;
+  double t, tau, tau_k, t_out;
+  int size, broken, m, ncomb;
+  int land, accept, out_idx, done;
+  int wnz[PMAX + 1];
+  int n_jv, n_sub, n_rej, m_last, m_max_used, status, replay_pos, attempts;
+  int n_iter, n_wjv, comb_terms, pad;
+};
+
+struct PhiArgs {
+  Tables T;
+  const double* u_lin;      // [4][ng] linearisation state (read-only)
+  const double* aux;        // [4][ng] eta and n x u of u_lin
+  double dt;
+  int p, ns;
+  double rho[NSMAX];
+  const double* v[PMAX + 1];   // device, nullptr = zero
+  double* y_out[NSMAX];
+  // workspace
+  double* Vbuf;             // (KMAX + 1) raw basis slots of n doubles (slot 0 unused)
+  double* W;                // (PMAX + 1) x n: W[0] = y_k, W[j] = w_j
+  double* tmp;              // 8 x ng pass-1 planes
+  double* part;             // nblocks x NRED partial sums
+  PhiCtrl* ctrl;
+  GridSync* sync;
+  DevStats* stats;          // accumulated (not reset by the kernel)
+  DevProfile* prof;         // nullable: operation counters
+  DevAttempt* trace;        // capacity trace_cap, appended at stats->n_trace
+  int trace_cap;
+  int call_index;
+  int* m_slot;              // nullable: initial m (if > 0), receives m_last
+  const double* replay;     // nullable device array, 3 doubles per attempt
+  int n_replay;
+  // options
+  double tol, delta, gamma, kappa;
+  int tol_mode, m_init, m_max, max_reject;
+  int64_t nA;
+};
+
+}  // namespace swe

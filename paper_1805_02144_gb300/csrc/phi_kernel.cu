@@ -1,0 +1,667 @@
+// phipm_simul_iom2 (Sec. 4.3, Algorithm 1) as one persistent, cooperatively
+// launched kernel: the w_j recurrence (Eq. eq3.18), the IOM2 Krylov sweep
+// (Algorithm 1 step 2(i)), the augmented exponential, error estimate and
+// substep controller (steps 2(ii)-6) and the substep update (Eq. eq3.17) all
+// run on the device; the host launches once per call.
+//
+// Work split: block b owns a contiguous range of cells (space-filling-curve
+// order, so its stencil gathers stay mostly inside the range).  Phases are
+// separated by bounded grid barriers; reductions are summed per block in a
+// fixed order, then over blocks in block order by the last block to arrive,
+// so results are bitwise reproducible for a given grid size.  The small
+// decisions (exponential of the (m+p+1)-square augmented matrix, controller)
+// run on one warp of block 0 while the other blocks wait at the barrier.
+//
+// The Krylov basis is stored unnormalised: raw slot j holds z_j (slot 0 is
+// w_p itself) and v_j = sig[j] * raw_j with sig[0] = 1/beta,
+// sig[j+1] = 1/h_{j+1,j}; every use folds the scale into its coefficients.
+#include <cuda_runtime.h>
+
+#include <cmath>
+
+#include "../../include/swe_exprb.h"
+#include "phi_args.h"
+#include "swe_dev.cuh"
+
+namespace swe {
+
+constexpr int PHI_THREADS = 256;
+constexpr double TAYLOR_THETA = 2.0;
+
+__device__ __forceinline__ double vld(const double* p) { return *(volatile const double*)p; }
+__device__ __forceinline__ int vldi(const int* p) { return *(volatile const int*)p; }
+
+struct Range {
+  int c0, c1;
+};
+
+// ---------------------------------------------------------------------------
+// block reductions in a fixed order
+// ---------------------------------------------------------------------------
+template <int K>
+__device__ __forceinline__ void block_sum(double (&v)[K], double* sred) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < K; ++k) sred[warp * NRED + k] = v[k];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < K; ++k) {
+      double s = 0.0;
+      for (int w = 0; w < PHI_THREADS / 32; ++w) s += sred[w * NRED + k];
+      v[k] = s;
+    }
+  }
+  __syncthreads();
+}
+
+struct Shared {
+  double red[(PHI_THREADS / 32) * NRED];
+  double coef[KMAX + PMAX + 4];
+  int last;
+  int ok;
+  unsigned int gen;
+  // decision scratch (block 0, warp 0)
+  double x[KMAX + PMAX + 8], y[KMAX + PMAX + 8], acc[KMAX + PMAX + 8];
+  double hd[KMAX + 1], hu[KMAX + 1], hl[KMAX + 2];
+};
+
+// Plain grid barrier.  Returns false (uniformly per block) when the launch is
+// being aborted.
+__device__ bool grid_barrier(const PhiArgs& a, Shared& sh) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    bool last;
+    unsigned int gen = bar_arrive(a.sync, gridDim.x, &last);
+    bool ok = true;
+    if (last)
+      bar_release(a.sync, gen);
+    else
+      ok = bar_wait(a.sync, gen, SWE_ERR_TIMEOUT);
+    sh.ok = ok && (ld_volatile_int(&a.sync->abort) == 0);
+  }
+  __syncthreads();
+  return sh.ok;
+}
+
+// Grid reduction of K per-thread partials, then a barrier.  The last block
+// to arrive sums the block partials in block order, stores them in
+// ctrl->red[], runs post(ctrl) on its thread 0, and releases the barrier.
+template <int K, class Post>
+__device__ bool grid_reduce(const PhiArgs& a, Shared& sh, double (&v)[K], Post post) {
+  block_sum<K>(v, sh.red);
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < K; ++k) a.part[(size_t)blockIdx.x * NRED + k] = v[k];
+    bool last;
+    sh.gen = bar_arrive(a.sync, gridDim.x, &last);
+    sh.last = last;
+  }
+  __syncthreads();
+  if (sh.last) {
+    double tot[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      double s = 0.0;
+      for (int b = threadIdx.x; b < (int)gridDim.x; b += PHI_THREADS) s += a.part[(size_t)b * NRED + k];
+      tot[k] = s;
+    }
+    block_sum<K>(tot, sh.red);
+    if (threadIdx.x == 0) {
+      volatile PhiCtrl* vc = a.ctrl;
+      for (int k = 0; k < K; ++k) vc->red[k] = tot[k];
+      post(vc);
+      bar_release(a.sync, sh.gen);
+      sh.ok = ld_volatile_int(&a.sync->abort) == 0;
+    }
+  } else if (threadIdx.x == 0) {
+    bool ok = bar_wait(a.sync, sh.gen, SWE_ERR_TIMEOUT);
+    sh.ok = ok && (ld_volatile_int(&a.sync->abort) == 0);
+  }
+  __syncthreads();
+  return sh.ok;
+}
+
+__device__ __forceinline__ void abort_launch(const PhiArgs& a, int code) {
+  atomicCAS(&a.sync->abort, 0, code);
+}
+
+__device__ __forceinline__ double* raw_slot(const PhiArgs& a, int j) {
+  const size_t n = (size_t)4 * a.T.ng;
+  return j == 0 ? a.W + (size_t)a.p * n : a.Vbuf + (size_t)j * n;
+}
+
+// ---------------------------------------------------------------------------
+// Augmented exponential by scaled Taylor series (one warp).
+// Hhat (size M = m+p+1): Hhat[0:m,0:m] = tau H_m (tridiagonal), Hhat[0,m] = 1,
+// Hhat[m+k, m+k+1] = 1 (k < p).  The last column of exp(Hhat) holds
+// phi_{p+1}(tau H) e_1 in its first m rows.  exp(Hhat) e_{M-1} =
+// (exp(Hhat/s))^s e_{M-1}, each factor a Taylor series summed until two
+// consecutive terms are below the double-precision unit roundoff relative to
+// the sum, with s = ceil(||Hhat||_1 / 2).
+// ---------------------------------------------------------------------------
+__device__ void taylor_phi(Shared& sh, int m, int p, double tau, double hnorm) {
+  const int lane = threadIdx.x;
+  const int M = m + p + 1;
+  const int s = (int)fmax(1.0, ceil(hnorm / TAYLOR_THETA));
+  const double inv_s = 1.0 / (double)s;
+  for (int r = lane; r < M; r += 32) sh.x[r] = (r == M - 1) ? 1.0 : 0.0;
+  __syncwarp();
+  for (int step = 0; step < s; ++step) {
+    for (int r = lane; r < M; r += 32) sh.acc[r] = sh.x[r];
+    __syncwarp();
+    double prev = INFINITY;
+    for (int k = 1; k <= 60; ++k) {
+      // y = (Hhat/s) x / k, written back into x
+      for (int r = lane; r < M; r += 32) {
+        double v;
+        if (r < m) {
+          v = sh.hd[r] * sh.x[r];
+          if (r > 0) v = fma(sh.hl[r], sh.x[r - 1], v);
+          if (r < m - 1) v = fma(sh.hu[r], sh.x[r + 1], v);
+          v *= tau;
+          if (r == 0) v += sh.x[m];
+        } else if (r < m + p) {
+          v = sh.x[r + 1];
+        } else {
+          v = 0.0;
+        }
+        sh.y[r] = v * (inv_s / (double)k);
+      }
+      __syncwarp();
+      double tn = 0.0, an = 0.0;
+      for (int r = lane; r < M; r += 32) {
+        double tv = sh.y[r];
+        sh.x[r] = tv;
+        double av = sh.acc[r] + tv;
+        sh.acc[r] = av;
+        tn = fmax(tn, fabs(tv));
+        an = fmax(an, fabs(av));
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        tn = fmax(tn, __shfl_xor_sync(0xffffffffu, tn, o));
+        an = fmax(an, __shfl_xor_sync(0xffffffffu, an, o));
+      }
+      __syncwarp();
+      if (tn + prev <= 1.1102230246251565e-16 * an) break;
+      prev = tn;
+    }
+    for (int r = lane; r < M; r += 32) sh.x[r] = sh.acc[r];
+    __syncwarp();
+  }
+  // sh.x[0:m] = phi_{p+1}(tau H) e_1;  phi_p(tau H) e_1 = tau H phi_{p+1} + e_1/p!  (Eq. eq3.7)
+  double fact = 1.0;
+  for (int k = 2; k <= p; ++k) fact *= k;
+  for (int r = lane; r < m; r += 32) {
+    double v = sh.hd[r] * sh.x[r];
+    if (r > 0) v = fma(sh.hl[r], sh.x[r - 1], v);
+    if (r < m - 1) v = fma(sh.hu[r], sh.x[r + 1], v);
+    v *= tau;
+    if (r == 0) v += 1.0 / fact;
+    sh.y[r] = v;
+  }
+  __syncwarp();
+}
+
+__device__ __forceinline__ long long nint_d(double x) { return (long long)floor(x + 0.5); }
+
+// C(tau, m) of Eq. eq:cost
+__device__ double cost_fn(double tau, int m, int p, double remaining, double N, double nA,
+                          double hnorm) {
+  long long nsub = nint_d(remaining / tau);
+  if (nsub < 1) nsub = 1;
+  long long e = nint_d(log2(hnorm / 5.37));
+  if (e < 0) e = 0;
+  double M = 44.0 / 3.0 + 2.0 * (double)e;
+  double mp = (double)(m + p + 1);
+  return (double)nsub * (double)m * (N + nA) + 2.0 * (p - 1) * (nA + N) + M * mp * mp * mp +
+         (2.0 * p + 1.0) * N;
+}
+
+// Error estimate, acceptance test and controller (Algorithm 1 steps 2(ii)-6),
+// executed by warp 0 of block 0.  Writes the decision into ctrl.
+__device__ void decide(const PhiArgs& a, Shared& sh) {
+  volatile PhiCtrl* C = a.ctrl;
+  const int lane = threadIdx.x;
+  const int p = a.p;
+  const double t = C->t, t_out = C->t_out;
+  const double remaining = t_out - t;
+  const double beta = C->beta;
+  double tau_nom;
+  int m;
+  int rec_acc = 0;
+  const bool replay = a.replay != nullptr;
+  if (replay) {
+    int pos = C->replay_pos;
+    if (pos >= a.n_replay) {
+      if (lane == 0) {
+        C->status = SWE_ERR_INVALID_ARG;
+        abort_launch(a, SWE_ERR_INVALID_ARG);
+      }
+      return;
+    }
+    tau_nom = a.replay[3 * pos];
+    m = (int)a.replay[3 * pos + 1];
+    rec_acc = a.replay[3 * pos + 2] != 0.0;
+  } else {
+    tau_nom = C->tau;
+    m = C->m;
+  }
+  const bool land = tau_nom >= remaining * (1.0 - 1e-12);
+  const double tau_k = land ? remaining : tau_nom;
+
+  int m_use = m;
+  double eps = 0.0, hnorm = 1.0, hnext = 0.0;
+  if (beta > 0.0) {
+    m_use = min(m, (int)C->size);
+    for (int r = lane; r <= m_use; r += 32) {
+      sh.hd[r] = C->hd[r];
+      sh.hu[r] = C->hu[r];
+      sh.hl[r] = C->hl[r];
+    }
+    __syncwarp();
+    double cs = 0.0;
+    for (int j = lane; j < m_use; j += 32) {
+      double s = fabs(sh.hd[j]);
+      if (j > 0) s += fabs(sh.hu[j - 1]);
+      if (j + 1 < m_use) s += fabs(sh.hl[j + 1]);
+      cs = fmax(cs, s);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) cs = fmax(cs, __shfl_xor_sync(0xffffffffu, cs, o));
+    hnorm = fmax(tau_k * cs, 1.0);
+    taylor_phi(sh, m_use, p, tau_k, hnorm);
+    hnext = (C->broken && m_use == C->size) ? 0.0 : sh.hl[m_use];
+    eps = pow(tau_k, (double)p) * beta * tau_k * fabs(hnext) * fabs(sh.x[m_use - 1]);
+  }
+  const double omega = t_out * eps / (tau_k * a.tol * C->scale);
+  const bool accepted = replay ? (rec_acc != 0) : (omega <= a.delta);
+
+  // combination coefficients (all lanes, then lane 0 finishes the scalars)
+  if (accepted) {
+    const double tp = pow(tau_k, (double)p);
+    if (beta > 0.0) {
+      for (int r = lane; r < m_use; r += 32) C->cV[r] = tp * beta * sh.y[r] * C->sig[r];
+      if (lane == 0)
+        C->cV[m_use] = hnext != 0.0 ? tp * beta * tau_k * hnext * sh.x[m_use - 1] * C->sig[m_use] : 0.0;
+    }
+  }
+  __syncwarp();
+  if (lane != 0) return;
+
+  // proposals (reading R8 of the oracle, the same arithmetic)
+  if (!isfinite(omega)) {
+    C->status = SWE_ERR_NONFINITE;
+    abort_launch(a, SWE_ERR_NONFINITE);
+    return;
+  }
+  const int cap = C->broken ? C->size : a.m_max;
+  double tau_new;
+  int m_new;
+  if (omega == 0.0) {
+    tau_new = 2.0 * tau_k;
+    m_new = max(1, (3 * m_use + 3) / 4);
+  } else {
+    double q = fmax(1.0, m_use / 4.0);
+    tau_new = tau_k * pow(omega / a.gamma, -1.0 / q);
+    tau_new = fmin(fmax(tau_new, tau_k / 5.0), 2.0 * tau_k);
+    int dm = (int)ceil(log(omega / a.gamma) / log(a.kappa));
+    m_new = m_use + dm;
+    m_new = min(max(m_new, (3 * m_use + 3) / 4), (m_use * 4) / 3 + 1);
+  }
+  m_new = max(1, min(min(m_new, a.m_max), cap));
+  const double N = 4.0 * (double)a.T.ng, nA = (double)a.nA;
+  double hnorm_new = 1.0;
+  if (beta > 0.0) {
+    // ||tau_new Hhat||_1 = max(tau_new * max column sum of |H_m|, 1)
+    double cs = 0.0;
+    for (int j = 0; j < m_use; ++j) {
+      double s = fabs(sh.hd[j]);
+      if (j > 0) s += fabs(sh.hu[j - 1]);
+      if (j + 1 < m_use) s += fabs(sh.hl[j + 1]);
+      cs = fmax(cs, s);
+    }
+    hnorm_new = fmax(tau_new * cs, 1.0);
+  }
+  const double c_tau = cost_fn(tau_new, m_use, p, remaining, N, nA, hnorm_new);
+  const double c_m = cost_fn(tau_k, m_new, p, remaining, N, nA, hnorm);
+  const bool take_tau = (c_tau <= c_m) || (!accepted && m_new == m_use);
+
+  // trace
+  {
+    DevStats* S = a.stats;
+    int idx = S->n_trace;
+    if (idx < a.trace_cap && a.trace != nullptr) {
+      DevAttempt& r = a.trace[idx];
+      r.t = t;
+      r.tau = tau_k;
+      r.omega = omega;
+      r.m = m_use;
+      r.accepted = accepted;
+      r.call = a.call_index;
+      r.pad = 0;
+    }
+    S->n_trace = idx + 1;
+  }
+  C->m_max_used = max(C->m_max_used, m_use);
+  C->attempts += 1;
+  if (replay) C->replay_pos += 1;
+  C->tau_k = tau_k;
+  C->land = land;
+  C->accept = accepted;
+  if (accepted) {
+    double f = 1.0;
+    for (int j = 0; j < p; ++j) {
+      if (j > 0) f *= (double)j;
+      C->cW[j] = pow(tau_k, (double)j) / f;
+    }
+    C->ncomb = beta > 0.0 ? m_use + 1 : 0;
+    C->comb_terms += C->ncomb + p;
+    C->t = land ? t_out : t + tau_k;
+    C->n_sub += 1;
+    if (take_tau) {
+      C->tau = land ? fmax(tau_new, tau_nom) : tau_new;
+    } else {
+      C->tau = land ? fmax(tau_k, tau_nom) : tau_k;
+      C->m = m_new;
+    }
+    C->m_last = m_use;
+  } else {
+    C->n_rej += 1;
+    if (C->n_rej > a.max_reject || tau_k < 1e-14) {
+      C->status = SWE_ERR_NOCONV;
+      abort_launch(a, SWE_ERR_NOCONV);
+      return;
+    }
+    if (take_tau) {
+      C->tau = tau_new;
+      C->m = m_use;
+    } else {
+      C->tau = tau_k;
+      C->m = m_new;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// the kernel
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(PHI_THREADS, 2) phi_kernel(const __grid_constant__ PhiArgs a) {
+  __shared__ Shared sh;
+  const Tables& T = a.T;
+  const int ng = T.ng;
+  const size_t n = (size_t)4 * ng;
+  const int p = a.p;
+  const int chunk = (ng + gridDim.x - 1) / gridDim.x;
+  const Range R{min(ng, (int)blockIdx.x * chunk), min(ng, ((int)blockIdx.x + 1) * chunk)};
+  PhiCtrl* C = a.ctrl;
+
+  // ---- prologue: y = v_0, norms of the inputs -----------------------------
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    C->status = SWE_OK;
+    C->n_jv = C->n_sub = C->n_rej = C->m_last = C->m_max_used = 0;
+    C->replay_pos = 0;
+    C->attempts = 0;
+    C->done = 0;
+    C->n_iter = C->n_wjv = C->comb_terms = 0;
+  }
+  {
+    double v[NRED];
+#pragma unroll
+    for (int k = 0; k < NRED; ++k) v[k] = 0.0;
+    for (int i = R.c0 + threadIdx.x; i < R.c1; i += PHI_THREADS) {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const size_t e = (size_t)c * ng + i;
+        double y0 = a.v[0] ? __ldg(a.v[0] + e) : 0.0;
+        a.W[e] = y0;
+        v[0] += (y0 != 0.0) ? 1.0 : 0.0;
+        for (int l = 0; l <= p; ++l)
+          if (a.v[l]) {
+            double x = __ldg(a.v[l] + e);
+            v[1 + l] = fma(x, x, v[1 + l]);
+          }
+      }
+    }
+    const int pp = p, tol_mode = a.tol_mode, m_max = a.m_max;
+    const double rho0 = a.rho[0];
+    const int m_init = (a.m_slot && *a.m_slot > 0) ? *a.m_slot : a.m_init;
+    auto post = [pp, tol_mode, m_max, rho0, m_init](volatile PhiCtrl* c) {
+      double mx = 0.0;
+      for (int l = 0; l <= pp; ++l) mx = fmax(mx, (double)c->red[1 + l]);
+      double scale = tol_mode == 0 ? sqrt(mx) : 1.0;
+      c->scale = scale;
+      c->wnz[0] = c->red[0] > 0.0;
+      c->t = 0.0;
+      c->tau = rho0;
+      c->m = max(1, min(m_init, m_max));
+      c->done = (scale == 0.0) || !isfinite(scale);
+      if (!isfinite(scale)) c->status = SWE_ERR_NONFINITE;
+    };
+    if (!grid_reduce<NRED>(a, sh, v, post)) goto finish;
+  }
+  if (vldi(&C->done)) {
+    for (int o = 0; o < a.ns; ++o)
+      for (int i = R.c0 + threadIdx.x; i < R.c1; i += PHI_THREADS)
+        for (int c = 0; c < 4; ++c) a.y_out[o][(size_t)c * ng + i] = 0.0;
+    goto finish;
+  }
+
+  for (int oi = 0; oi < a.ns; ++oi) {
+    const double t_out = a.rho[oi];
+    if (blockIdx.x == 0 && threadIdx.x == 0) C->t_out = t_out;
+    while (vld(&C->t) < t_out) {
+      // ---- step 1: w_j = A w_{j-1} + sum_l t^l/l! v_{j+l}  (Eq. eq3.18) ----
+      const double t = vld(&C->t);
+      for (int j = 1; j <= p; ++j) {
+        double cl[PMAX + 1];
+        {
+          double f = 1.0, tp = 1.0;
+          for (int l = 0; l <= p - j; ++l) {
+            if (l > 0) {
+              f *= (double)l;
+              tp *= t;
+            }
+            cl[l] = tp / f;
+          }
+        }
+        const bool nz_prev = vldi(&C->wnz[j - 1]) != 0;
+        double* wprev = a.W + (size_t)(j - 1) * n;
+        double* wj = a.W + (size_t)j * n;
+        if (nz_prev) {
+          for (int i = R.c0 + threadIdx.x; i < R.c1; i += PHI_THREADS)
+            pass1_cell<MODE_J>(T, i, wprev, 1.0, a.u_lin, a.tmp);
+          if (!grid_barrier(a, sh)) goto finish;
+        }
+        double v[2] = {0.0, 0.0};
+        for (int i = R.c0 + threadIdx.x; i < R.c1; i += PHI_THREADS) {
+          double o[4] = {0.0, 0.0, 0.0, 0.0};
+          if (nz_prev) pass2_cell<MODE_J>(T, i, wprev, 1.0, a.tmp, a.aux, o);
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const size_t e = (size_t)c * ng + i;
+            double w = a.dt * o[c];
+            for (int l = 0; l <= p - j; ++l)
+              if (a.v[j + l]) w = fma(cl[l], __ldg(a.v[j + l] + e), w);
+            wj[e] = w;
+            v[0] += (w != 0.0) ? 1.0 : 0.0;
+            v[1] = fma(w, w, v[1]);
+          }
+        }
+        GridSync* gs = a.sync;
+        auto post = [gs, j, nz_prev, p](volatile PhiCtrl* c) {
+          c->wnz[j] = c->red[0] > 0.0;
+          if (nz_prev) {
+            c->n_jv += 1;
+            c->n_wjv += 1;
+          }
+          if (j == p) {
+            double b = sqrt((double)c->red[1]);
+            c->beta = b;
+            c->sig[0] = b > 0.0 ? 1.0 / b : 0.0;
+            c->size = 0;
+            c->broken = 0;
+            if (!isfinite(b)) {
+              c->status = SWE_ERR_NONFINITE;
+              atomicCAS(&gs->abort, 0, SWE_ERR_NONFINITE);
+            }
+          }
+        };
+        if (!grid_reduce<2>(a, sh, v, post)) goto finish;
+      }
+
+      // ---- attempts on this substep ---------------------------------------
+      while (true) {
+        const double beta = vld(&C->beta);
+        if (beta > 0.0) {
+          int m_req;
+          if (a.replay) {
+            int pos = vldi(&C->replay_pos);
+            m_req = pos < a.n_replay ? (int)a.replay[3 * pos + 1] : 1;
+          } else {
+            m_req = vldi(&C->m);
+          }
+          m_req = min(m_req, KMAX);
+          // ---- IOM2: extend the basis to m_req columns (step 2(i)) --------
+          while (vldi(&C->size) < m_req && !vldi(&C->broken)) {
+            const int j = vldi(&C->size);
+            double* rj = raw_slot(a, j);
+            double* rj1 = raw_slot(a, j + 1);
+            double* rjm = j > 0 ? raw_slot(a, j - 1) : nullptr;
+            const double sj = vld(&C->sig[j]);
+            for (int i = R.c0 + threadIdx.x; i < R.c1; i += PHI_THREADS)
+              pass1_cell<MODE_J>(T, i, rj, sj, a.u_lin, a.tmp);
+            if (!grid_barrier(a, sh)) goto finish;
+            double v[2] = {0.0, 0.0};
+            for (int i = R.c0 + threadIdx.x; i < R.c1; i += PHI_THREADS) {
+              double o[4];
+              pass2_cell<MODE_J>(T, i, rj, sj, a.tmp, a.aux, o);
+#pragma unroll
+              for (int c = 0; c < 4; ++c) {
+                const size_t e = (size_t)c * ng + i;
+                double z = a.dt * o[c];
+                rj1[e] = z;
+                if (rjm) v[0] = fma(z, rjm[e], v[0]);
+                v[1] = fma(z, rj[e], v[1]);
+              }
+            }
+            auto post_dots = [j](volatile PhiCtrl* c) {
+              if (j > 0) c->hu[j - 1] = c->sig[j - 1] * c->red[0];
+              c->hd[j] = c->sig[j] * c->red[1];
+            };
+            if (!grid_reduce<2>(a, sh, v, post_dots)) goto finish;
+            // z <- z - h_{j-1,j} v_{j-1} - h_{j,j} v_j, and its norm
+            const double cm = j > 0 ? vld(&C->hu[j - 1]) * vld(&C->sig[j - 1]) : 0.0;
+            const double cj = vld(&C->hd[j]) * sj;
+            double w[1] = {0.0};
+            for (int i = R.c0 + threadIdx.x; i < R.c1; i += PHI_THREADS) {
+#pragma unroll
+              for (int c = 0; c < 4; ++c) {
+                const size_t e = (size_t)c * ng + i;
+                double z = fma(-cj, rj[e], rj1[e]);
+                if (rjm) z = fma(-cm, rjm[e], z);
+                rj1[e] = z;
+                w[0] = fma(z, z, w[0]);
+              }
+            }
+            GridSync* gs = a.sync;
+            auto post_norm = [gs, j](volatile PhiCtrl* c) {
+              double hn = sqrt((double)c->red[0]);
+              double ref = fabs((double)c->hd[j]) + (j > 0 ? fabs((double)c->hu[j - 1]) : 0.0);
+              c->size = j + 1;
+              c->n_jv += 1;
+              c->n_iter += 1;
+              if (!isfinite(hn) || !isfinite(ref)) {
+                c->status = SWE_ERR_NONFINITE;
+                atomicCAS(&gs->abort, 0, SWE_ERR_NONFINITE);
+                return;
+              }
+              if (hn <= 1e-13 * ref) {  // happy breakdown: invariant subspace
+                c->broken = 1;
+                c->hl[j + 1] = 0.0;
+                c->sig[j + 1] = 0.0;
+              } else {
+                c->hl[j + 1] = hn;
+                c->sig[j + 1] = 1.0 / hn;
+              }
+            };
+            if (!grid_reduce<1>(a, sh, w, post_norm)) goto finish;
+          }
+        }
+        // ---- exponential, error estimate, controller (steps 2(ii)-6) -------
+        if (blockIdx.x == 0 && threadIdx.x < 32) decide(a, sh);
+        if (!grid_barrier(a, sh)) goto finish;
+        if (!vldi(&C->accept)) continue;
+
+        // ---- y_{k+1} = tau^p phi_p(tau A) w_p + sum_{j<p} tau^j/j! w_j (eq3.17)
+        const int ncomb = vldi(&C->ncomb);
+        for (int r = threadIdx.x; r < ncomb; r += PHI_THREADS) sh.coef[r] = vld(&C->cV[r]);
+        for (int r = threadIdx.x; r < p; r += PHI_THREADS) sh.coef[KMAX + 2 + r] = vld(&C->cW[r]);
+        __syncthreads();
+        const bool land = vldi(&C->land) != 0;
+        double* yo = land ? a.y_out[oi] : nullptr;
+        double v[1] = {0.0};
+        for (int i = R.c0 + threadIdx.x; i < R.c1; i += PHI_THREADS) {
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const size_t e = (size_t)c * ng + i;
+            double y = 0.0;
+            for (int j = 0; j < p; ++j) y = fma(sh.coef[KMAX + 2 + j], a.W[(size_t)j * n + e], y);
+            for (int r = 0; r < ncomb; ++r) y = fma(sh.coef[r], raw_slot(a, r)[e], y);
+            a.W[e] = y;
+            if (yo) yo[e] = y;
+            v[0] += (y != 0.0) ? 1.0 : 0.0;
+          }
+        }
+        auto post_y = [](volatile PhiCtrl* c) { c->wnz[0] = c->red[0] > 0.0; };
+        if (!grid_reduce<1>(a, sh, v, post_y)) goto finish;
+        break;
+      }
+    }
+  }
+
+finish:
+  // The last writer of the statistics is block 0 once everything has stopped.
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    DevStats* S = a.stats;
+    int ab = ld_volatile_int(&a.sync->abort);
+    int st = C->status != SWE_OK ? C->status : ab;
+    S->n_jv += C->n_jv;
+    S->n_sub += C->n_sub;
+    S->n_rej += C->n_rej;
+    S->m_last = C->m_last;
+    S->m_max_used = max(S->m_max_used, C->m_max_used);
+    if (S->status == SWE_OK) S->status = st;
+    if (a.m_slot && st == SWE_OK && C->m_last > 0) *a.m_slot = C->m_last;
+    if (a.prof) {
+      a.prof->iters += C->n_iter;
+      a.prof->wjv += C->n_wjv;
+      a.prof->comb_terms += C->comb_terms;
+      a.prof->launches += 1;
+    }
+  }
+}
+
+int launch_phi_kernel(const PhiArgs& a, int nblocks, cudaStream_t stream) {
+  void* args[] = {(void*)&a};
+  cudaError_t e = cudaLaunchCooperativeKernel((void*)phi_kernel, dim3(nblocks), dim3(PHI_THREADS),
+                                              args, 0, stream);
+  return e == cudaSuccess ? 0 : (int)e;
+}
+
+int phi_kernel_max_blocks(int* nblocks) {
+  int dev = 0, nsm = 0, per = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, phi_kernel, PHI_THREADS, 0) != cudaSuccess)
+    return -1;
+  if (per < 1) return -1;
+  *nblocks = nsm * per;
+  return 0;
+}
+
+}  // namespace swe

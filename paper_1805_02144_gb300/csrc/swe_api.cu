@@ -1,0 +1,756 @@
+// C ABI of the library (include/swe_exprb.h): grid handles, the F / J x
+// stencil kernels, phi_action (one persistent launch of phipm_simul_iom2) and
+// the exprb_step drivers of Sec. 4.4.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/swe_exprb.h"
+#include "grid_build.h"
+#include "phi_args.h"
+#include "swe_dev.cuh"
+
+namespace swe {
+int launch_phi_kernel(const PhiArgs& a, int nblocks, cudaStream_t stream);
+int phi_kernel_max_blocks(int* nblocks);
+}  // namespace swe
+
+using namespace swe;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(SWE_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+#define CK(call)                                   \
+  do {                                             \
+    cudaError_t e_ = (call);                       \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+constexpr int TRACE_CAP = 4096;
+constexpr int STAGE_VECS = 12;
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// grid handle
+// ---------------------------------------------------------------------------
+struct swe_grid {
+  HostGrid host;
+  Tables T;
+  int device = 0;
+  void* dtab = nullptr;      // one allocation for all tables
+  // workspace (lazily allocated)
+  void* dws = nullptr;
+  size_t ws_bytes = 0;
+  double* Vbuf = nullptr;
+  double* W = nullptr;
+  double* tmp = nullptr;
+  double* tmp2 = nullptr;
+  double* aux = nullptr;
+  double* part = nullptr;
+  double* stage = nullptr;   // STAGE_VECS vectors of n
+  PhiCtrl* ctrl = nullptr;
+  GridSync* sync = nullptr;
+  DevStats* stats = nullptr;
+  DevAttempt* trace = nullptr;
+  double* replay = nullptr;
+  int replay_cap = 0;
+  int nblocks = 0;
+  // profiling (swe_profile_enable)
+  bool prof_on = false;
+  DevProfile* dprof = nullptr;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> phi_ev, call_ev;
+  int64_t kernel_launches = 0;
+};
+
+struct swe_scheme_state {
+  const swe_grid* grid = nullptr;
+  double* u_prev = nullptr;  // epi3 history (device)
+  int* m_slots = nullptr;    // device ints, one per call slot
+  int have_prev = 0;
+};
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// standalone kernels
+// ---------------------------------------------------------------------------
+constexpr int TPB = 256;
+
+__global__ void k_aux(Tables T, const double* __restrict__ u, double* aux) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < T.ng; i += gridDim.x * blockDim.x)
+    aux_cell(T, i, u, aux);
+}
+
+template <int MODE>
+__global__ void k_pass1(Tables T, const double* x, double sx, const double* u, double* tmp) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < T.ng; i += gridDim.x * blockDim.x)
+    pass1_cell<MODE>(T, i, x, sx, u, tmp);
+}
+
+// out = alpha * stencil(x)  (+ beta_ * add, when add != nullptr)
+template <int MODE>
+__global__ void k_pass2(Tables T, const double* x, double sx, const double* tmp, const double* aux,
+                        double alpha, double* out) {
+  const int ng = T.ng;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ng; i += gridDim.x * blockDim.x) {
+    double o[4];
+    pass2_cell<MODE>(T, i, x, sx, tmp, aux, o);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) out[(size_t)c * ng + i] = alpha * o[c];
+  }
+}
+
+struct Comb {
+  const double* x[6];
+  double c[6];
+  int k;
+};
+
+// out = sum_k c_k x_k over n elements
+__global__ void k_lincomb(size_t n, Comb cb, double* out) {
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int k = 0; k < cb.k; ++k) s = fma(cb.c[k], cb.x[k][e], s);
+    out[e] = s;
+  }
+}
+
+int grid_blocks(size_t work) {
+  size_t b = (work + TPB - 1) / TPB;
+  if (b > 152 * 16) b = 152 * 16;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+cudaStream_t S(void* s) { return (cudaStream_t)s; }
+
+cudaEvent_t prof_event(const swe_grid* gc) {
+  swe_grid* g = const_cast<swe_grid*>(gc);
+  if (g->ev_used == g->ev_pool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    g->ev_pool.push_back(e);
+  }
+  return g->ev_pool[g->ev_used++];
+}
+
+void count_launches(const swe_grid* gc, int k) {
+  swe_grid* g = const_cast<swe_grid*>(gc);
+  if (g->prof_on) g->kernel_launches += k;
+}
+
+// Records a start event when profiling; finish() records the end and keeps the pair.
+struct ProfSpan {
+  swe_grid* g;
+  cudaStream_t st;
+  cudaEvent_t a = nullptr;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>>* list;
+  ProfSpan(swe_grid* g_, cudaStream_t st_, std::vector<std::pair<cudaEvent_t, cudaEvent_t>>* l)
+      : g(g_), st(st_), list(l) {
+    if (g->prof_on && (a = prof_event(g))) cudaEventRecord(a, st);
+  }
+  void finish() {
+    if (!a) return;
+    cudaEvent_t b = prof_event(g);
+    if (!b) return;
+    cudaEventRecord(b, st);
+    list->push_back({a, b});
+    a = nullptr;
+  }
+};
+
+int run_rhs(const swe_grid* g, const double* u, double* f, double alpha, cudaStream_t st) {
+  const Tables& T = g->T;
+  int nb = grid_blocks(T.ng);
+  k_pass1<MODE_F><<<nb, TPB, 0, st>>>(T, u, 1.0, nullptr, g->tmp2);
+  k_pass2<MODE_F><<<nb, TPB, 0, st>>>(T, u, 1.0, g->tmp2, nullptr, alpha, f);
+  CK(cudaGetLastError());
+  count_launches(g, 2);
+  return SWE_OK;
+}
+
+int run_quad(const swe_grid* g, const double* d, double* out, double alpha, cudaStream_t st) {
+  const Tables& T = g->T;
+  int nb = grid_blocks(T.ng);
+  k_pass1<MODE_Q><<<nb, TPB, 0, st>>>(T, d, 1.0, nullptr, g->tmp2);
+  k_pass2<MODE_Q><<<nb, TPB, 0, st>>>(T, d, 1.0, g->tmp2, nullptr, alpha, out);
+  CK(cudaGetLastError());
+  count_launches(g, 2);
+  return SWE_OK;
+}
+
+int run_lincomb(const swe_grid* g, double* out, std::initializer_list<std::pair<double, const double*>> terms,
+                cudaStream_t st) {
+  Comb cb{};
+  cb.k = 0;
+  for (auto& t : terms) {
+    if (cb.k == 6) return fail(SWE_ERR_INVALID_ARG, "lincomb: too many terms");
+    cb.c[cb.k] = t.first;
+    cb.x[cb.k] = t.second;
+    cb.k++;
+  }
+  size_t n = (size_t)4 * g->T.ng;
+  k_lincomb<<<grid_blocks(n), TPB, 0, st>>>(n, cb, out);
+  CK(cudaGetLastError());
+  count_launches(g, 1);
+  return SWE_OK;
+}
+
+int upload_grid(swe_grid* g) {
+  HostGrid& h = g->host;
+  const size_t ng = h.ng;
+  struct Part {
+    const void* src;
+    size_t bytes;
+    void** dst;
+  };
+  const int32_t* d_nbr = nullptr;
+  const double *d_nrm = nullptr, *d_wl = nullptr, *d_wld = nullptr, *d_nc = nullptr, *d_ndd = nullptr,
+               *d_sdg = nullptr, *d_vc = nullptr, *d_vd = nullptr;
+  Part parts[] = {
+      {h.nbr.data(), h.nbr.size() * 4, (void**)&d_nbr},  {h.xyz.data(), h.xyz.size() * 8, (void**)&d_nrm},
+      {h.wl.data(), h.wl.size() * 8, (void**)&d_wl},     {h.wld.data(), h.wld.size() * 8, (void**)&d_wld},
+      {h.nc.data(), h.nc.size() * 8, (void**)&d_nc},     {h.ndd.data(), h.ndd.size() * 8, (void**)&d_ndd},
+      {h.sdg.data(), h.sdg.size() * 8, (void**)&d_sdg},  {h.vc.data(), h.vc.size() * 8, (void**)&d_vc},
+      {h.vd.data(), h.vd.size() * 8, (void**)&d_vd},
+  };
+  size_t total = 0;
+  for (auto& p : parts) total += (p.bytes + 255) & ~size_t(255);
+  CK(cudaMalloc(&g->dtab, total));
+  size_t off = 0;
+  for (auto& p : parts) {
+    char* dst = (char*)g->dtab + off;
+    CK(cudaMemcpy(dst, p.src, p.bytes, cudaMemcpyHostToDevice));
+    *p.dst = dst;
+    off += (p.bytes + 255) & ~size_t(255);
+  }
+  (void)ng;
+  Tables& T = g->T;
+  T.nbr = d_nbr;
+  T.nrm = d_nrm;
+  T.wl = d_wl;
+  T.wld = d_wld;
+  T.nc = d_nc;
+  T.ndd = d_ndd;
+  T.sdg = d_sdg;
+  T.vc = d_vc;
+  T.vd = d_vd;
+  return SWE_OK;
+}
+
+int ensure_workspace(swe_grid* g) {
+  if (!g->dtab) return fail(SWE_ERR_INVALID_ARG, "grid was built on the host only");
+  if (g->dws) return SWE_OK;
+  int nb = 0;
+  if (phi_kernel_max_blocks(&nb) != 0) return fail(SWE_ERR_CUDA, "occupancy query for phi kernel failed");
+  g->nblocks = nb;
+  const size_t ng = g->T.ng, n = 4 * ng;
+  size_t sizes[] = {
+      (size_t)(KMAX + 1) * n * 8,  // Vbuf
+      (size_t)(PMAX + 1) * n * 8,  // W
+      8 * ng * 8,                  // tmp
+      8 * ng * 8,                  // tmp2
+      4 * ng * 8,                  // aux
+      (size_t)nb * NRED * 8,       // part
+      (size_t)STAGE_VECS * n * 8,  // stage
+      sizeof(PhiCtrl), sizeof(GridSync), sizeof(DevStats), (size_t)TRACE_CAP * sizeof(DevAttempt),
+      sizeof(DevProfile)};
+  size_t total = 0;
+  for (size_t s : sizes) total += (s + 255) & ~size_t(255);
+  cudaError_t e = cudaMalloc(&g->dws, total);
+  if (e != cudaSuccess) {
+    g->dws = nullptr;
+    return fail(SWE_ERR_NOMEM, std::string("workspace allocation failed: ") + cudaGetErrorString(e));
+  }
+  char* p = (char*)g->dws;
+  void** dst[] = {(void**)&g->Vbuf, (void**)&g->W,     (void**)&g->tmp,   (void**)&g->tmp2,
+                  (void**)&g->aux,  (void**)&g->part,  (void**)&g->stage, (void**)&g->ctrl,
+                  (void**)&g->sync, (void**)&g->stats, (void**)&g->trace, (void**)&g->dprof};
+  for (int k = 0; k < 12; ++k) {
+    *dst[k] = p;
+    p += (sizes[k] + 255) & ~size_t(255);
+  }
+  g->ws_bytes = total;
+  CK(cudaMemset(g->dws, 0, total));
+  return SWE_OK;
+}
+
+int resolve_opts(const phi_opts* in, phi_opts& o) {
+  if (in)
+    o = *in;
+  else
+    swe_phi_opts_default(&o);
+  if (!(o.tol > 0.0) || o.m_init < 1 || o.m_max < 1 || o.m_max > KMAX || o.iom != 2 ||
+      !(o.delta > 0.0) || !(o.gamma > 0.0) || !(o.kappa > 1.0) || o.max_reject < 0 ||
+      (o.tol_mode != 0 && o.tol_mode != 1) || (o.replay && o.n_replay < 1))
+    return fail(SWE_ERR_INVALID_ARG, "invalid phi_opts (m_max <= 64, iom == 2, tol > 0, kappa > 1)");
+  return SWE_OK;
+}
+
+int stage_replay(swe_grid* g, const phi_opts& o, cudaStream_t st) {
+  if (!o.replay) return SWE_OK;
+  if (o.n_replay > g->replay_cap) {
+    if (g->replay) cudaFree(g->replay);
+    g->replay = nullptr;
+    CK(cudaMalloc(&g->replay, (size_t)o.n_replay * 3 * sizeof(double)));
+    g->replay_cap = o.n_replay;
+  }
+  CK(cudaMemcpyAsync(g->replay, o.replay, (size_t)o.n_replay * 3 * sizeof(double), cudaMemcpyHostToDevice, st));
+  return SWE_OK;
+}
+
+// One phipm_simul_iom2 evaluation; aux of u_lin must already be in g->aux.
+int phi_call(swe_grid* g, const double* u_lin, double dt, int p, const double* const* v, int ns,
+             const double* rho, double* const* y_out, const phi_opts& o, int call_index, int* m_slot,
+             int replay_offset, cudaStream_t st) {
+  PhiArgs a{};
+  a.T = g->T;
+  a.u_lin = u_lin;
+  a.aux = g->aux;
+  a.dt = dt;
+  a.p = p;
+  a.ns = ns;
+  for (int i = 0; i < ns; ++i) {
+    a.rho[i] = rho[i];
+    a.y_out[i] = y_out[i];
+  }
+  for (int l = 0; l <= p; ++l) a.v[l] = v[l];
+  a.Vbuf = g->Vbuf;
+  a.W = g->W;
+  a.tmp = g->tmp;
+  a.part = g->part;
+  a.ctrl = g->ctrl;
+  a.sync = g->sync;
+  a.stats = g->stats;
+  a.trace = g->trace;
+  a.trace_cap = TRACE_CAP;
+  a.call_index = call_index;
+  a.m_slot = m_slot;
+  a.replay = o.replay ? g->replay + 3 * (size_t)replay_offset : nullptr;
+  a.n_replay = o.replay ? o.n_replay - replay_offset : 0;
+  a.tol = o.tol;
+  a.delta = o.delta;
+  a.gamma = o.gamma;
+  a.kappa = o.kappa;
+  a.tol_mode = o.tol_mode;
+  a.m_init = o.m_init;
+  a.m_max = o.m_max;
+  a.max_reject = o.max_reject;
+  a.nA = g->host.nA;
+  a.prof = g->prof_on ? g->dprof : nullptr;
+  CK(cudaMemsetAsync(g->sync, 0, sizeof(GridSync), st));
+  ProfSpan span(g, st, &g->phi_ev);
+  int e = launch_phi_kernel(a, g->nblocks, st);
+  if (e != 0) return cuda_fail((cudaError_t)e, "cudaLaunchCooperativeKernel(phi_kernel)");
+  span.finish();
+  count_launches(g, 1);
+  return SWE_OK;
+}
+
+int validate_phi_args(int p, const double* const* v, int ns, const double* rho, double* const* y_out) {
+  if (p < 1 || p > PMAX) return fail(SWE_ERR_INVALID_ARG, "p must be in [1, 4]");
+  if (ns < 1 || ns > NSMAX) return fail(SWE_ERR_INVALID_ARG, "ns must be in [1, 8]");
+  if (!v || !rho || !y_out) return fail(SWE_ERR_INVALID_ARG, "v, rho and y_out are required");
+  if (!(rho[0] > 0.0) || !(rho[ns - 1] <= 1.0)) return fail(SWE_ERR_INVALID_ARG, "rho must lie in (0, 1]");
+  for (int i = 1; i < ns; ++i)
+    if (!(rho[i] > rho[i - 1])) return fail(SWE_ERR_INVALID_ARG, "rho must be increasing");
+  for (int i = 0; i < ns; ++i)
+    if (!y_out[i]) return fail(SWE_ERR_INVALID_ARG, "y_out entries must be non-NULL");
+  return SWE_OK;
+}
+
+int read_stats(swe_grid* g, phi_stats* stats, cudaStream_t st) {
+  if (!stats) return SWE_OK;
+  DevStats ds;
+  CK(cudaMemcpyAsync(&ds, g->stats, sizeof(DevStats), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  stats->n_jv = ds.n_jv;
+  stats->n_substeps = ds.n_sub;
+  stats->n_reject = ds.n_rej;
+  stats->m_last = ds.m_last;
+  stats->m_max_used = ds.m_max_used;
+  stats->status = ds.status;
+  int nt = ds.n_trace < TRACE_CAP ? ds.n_trace : TRACE_CAP;
+  stats->n_trace = 0;
+  if (stats->trace && stats->trace_cap > 0) {
+    int k = nt < stats->trace_cap ? nt : stats->trace_cap;
+    if (k > 0) {
+      static_assert(sizeof(DevAttempt) == sizeof(phi_attempt), "trace record layout");
+      CK(cudaMemcpy(stats->trace, g->trace, (size_t)k * sizeof(DevAttempt), cudaMemcpyDeviceToHost));
+    }
+    stats->n_trace = k;
+  }
+  return SWE_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// public entry points
+// ---------------------------------------------------------------------------
+extern "C" {
+
+void swe_phi_opts_default(phi_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->tol = 1e-8;
+  o->tol_mode = 0;
+  o->m_init = 1;
+  o->m_max = 64;
+  o->iom = 2;
+  o->delta = 1.4;
+  o->gamma = 0.8;
+  o->kappa = 2.0;
+  o->max_reject = 200;
+  o->m_carry = 1;
+  o->replay = nullptr;
+  o->n_replay = 0;
+}
+
+const char* swe_last_error(void) { return g_last_error.c_str(); }
+
+static int create_grid(int level, double radius, double g, double omega, double gamma_h, int reorder,
+                       bool device, swe_grid** out) {
+  if (!out) return fail(SWE_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!(radius > 0.0) || !(g > 0.0) || !(gamma_h >= 0.0) || !std::isfinite(omega))
+    return fail(SWE_ERR_INVALID_ARG, "radius, g must be > 0 and gamma_h >= 0");
+  swe_grid* G = new (std::nothrow) swe_grid();
+  if (!G) return fail(SWE_ERR_NOMEM, "host allocation failed");
+  const char* err = nullptr;
+  if (build_host_grid(level, radius, reorder != 0, G->host, &err) != 0) {
+    delete G;
+    return fail(SWE_ERR_INVALID_ARG, err ? err : "grid construction failed");
+  }
+  const int ng = G->host.ng;
+  double dx = std::sqrt(4.0 * M_PI * radius * radius / ng);
+  G->T.ng = ng;
+  G->T.nu = gamma_h * dx * dx * dx * dx / 240.0;  // Eq. eq:niu, n_gamma = 4, dt_e = 240 s
+  G->T.g = g;
+  G->T.two_omega = 2.0 * omega;
+  if (!device) {
+    *out = G;
+    return SWE_OK;
+  }
+  cudaGetDevice(&G->device);
+  int rc = upload_grid(G);
+  if (rc != SWE_OK) {
+    if (G->dtab) cudaFree(G->dtab);
+    delete G;
+    return rc;
+  }
+  *out = G;
+  return SWE_OK;
+}
+
+int swe_create_grid(int level, double radius, double g, double omega, double gamma_h, int reorder,
+                    swe_grid** out) {
+  return create_grid(level, radius, g, omega, gamma_h, reorder, true, out);
+}
+
+int swe_create_grid_host(int level, double radius, double g, double omega, double gamma_h,
+                         int reorder, swe_grid** out) {
+  return create_grid(level, radius, g, omega, gamma_h, reorder, false, out);
+}
+
+int swe_grid_export(const swe_grid* g, const char* table, void* out, int64_t count) {
+  if (!g || !table || !out) return fail(SWE_ERR_INVALID_ARG, "grid, table and out are required");
+  const HostGrid& h = g->host;
+  auto put = [&](const void* src, size_t elems, size_t esz) {
+    if ((int64_t)elems != count) return fail(SWE_ERR_INVALID_ARG, std::string("count mismatch for ") + table);
+    std::memcpy(out, src, elems * esz);
+    return (int)SWE_OK;
+  };
+  std::string t(table);
+  if (t == "nbr") return put(h.nbr.data(), h.nbr.size(), 4);
+  if (t == "wl") return put(h.wl.data(), h.wl.size(), 8);
+  if (t == "wld") return put(h.wld.data(), h.wld.size(), 8);
+  if (t == "nc") return put(h.nc.data(), h.nc.size(), 8);
+  if (t == "ndd") return put(h.ndd.data(), h.ndd.size(), 8);
+  if (t == "sdg") return put(h.sdg.data(), h.sdg.size(), 8);
+  if (t == "vc") return put(h.vc.data(), h.vc.size(), 8);
+  if (t == "vd") return put(h.vd.data(), h.vd.size(), 8);
+  return fail(SWE_ERR_INVALID_ARG, std::string("unknown table ") + table);
+}
+
+void swe_destroy_grid(swe_grid* g) {
+  if (!g) return;
+  for (cudaEvent_t e : g->ev_pool) cudaEventDestroy(e);
+  if (g->dtab) cudaFree(g->dtab);
+  if (g->dws) cudaFree(g->dws);
+  if (g->replay) cudaFree(g->replay);
+  delete g;
+}
+
+int swe_grid_query(const swe_grid* g, int64_t* ncells, int64_t* n, int64_t* nA, double* nu) {
+  if (!g) return fail(SWE_ERR_INVALID_ARG, "grid is NULL");
+  if (ncells) *ncells = g->host.ng;
+  if (n) *n = 4 * (int64_t)g->host.ng;
+  if (nA) *nA = g->host.nA;
+  if (nu) *nu = g->T.nu;
+  return SWE_OK;
+}
+
+int swe_grid_cell_centres(const swe_grid* g, double* xyz) {
+  if (!g || !xyz) return fail(SWE_ERR_INVALID_ARG, "grid and xyz are required");
+  std::memcpy(xyz, g->host.xyz.data(), g->host.xyz.size() * sizeof(double));
+  return SWE_OK;
+}
+
+int swe_grid_cell_areas(const swe_grid* g, double* area) {
+  if (!g || !area) return fail(SWE_ERR_INVALID_ARG, "grid and area are required");
+  std::memcpy(area, g->host.area.data(), g->host.area.size() * sizeof(double));
+  return SWE_OK;
+}
+
+int swe_rhs(const swe_grid* gc, const double* u, double* f, void* stream) {
+  swe_grid* g = const_cast<swe_grid*>(gc);
+  if (!g || !u || !f) return fail(SWE_ERR_INVALID_ARG, "swe_rhs: NULL argument");
+  int rc = ensure_workspace(g);
+  if (rc) return rc;
+  return run_rhs(g, u, f, 1.0, S(stream));
+}
+
+int swe_jv(const swe_grid* gc, const double* u, const double* x, double* jx, void* stream) {
+  swe_grid* g = const_cast<swe_grid*>(gc);
+  if (!g || !u || !x || !jx) return fail(SWE_ERR_INVALID_ARG, "swe_jv: NULL argument");
+  int rc = ensure_workspace(g);
+  if (rc) return rc;
+  const Tables& T = g->T;
+  cudaStream_t st = S(stream);
+  int nb = grid_blocks(T.ng);
+  k_aux<<<nb, TPB, 0, st>>>(T, u, g->aux);
+  k_pass1<MODE_J><<<nb, TPB, 0, st>>>(T, x, 1.0, u, g->tmp2);
+  k_pass2<MODE_J><<<nb, TPB, 0, st>>>(T, x, 1.0, g->tmp2, g->aux, 1.0, jx);
+  CK(cudaGetLastError());
+  count_launches(g, 3);
+  return SWE_OK;
+}
+
+int phi_action(swe_grid* g, const double* u_lin, double dt, int p, const double* const* v, int ns,
+               const double* rho, double* const* y_out, const phi_opts* opts, phi_stats* stats,
+               void* stream) {
+  if (!g || !u_lin) return fail(SWE_ERR_INVALID_ARG, "phi_action: NULL grid or u_lin");
+  int rc = validate_phi_args(p, v, ns, rho, y_out);
+  if (rc) return rc;
+  phi_opts o;
+  if ((rc = resolve_opts(opts, o))) return rc;
+  if ((rc = ensure_workspace(g))) return rc;
+  cudaStream_t st = S(stream);
+  if ((rc = stage_replay(g, o, st))) return rc;
+  ProfSpan span(g, st, &g->call_ev);
+  CK(cudaMemsetAsync(g->stats, 0, sizeof(DevStats), st));
+  k_aux<<<grid_blocks(g->T.ng), TPB, 0, st>>>(g->T, u_lin, g->aux);
+  CK(cudaGetLastError());
+  count_launches(g, 1);
+  if ((rc = phi_call(g, u_lin, dt, p, v, ns, rho, y_out, o, 0, nullptr, 0, st))) return rc;
+  span.finish();
+  return read_stats(g, stats, st);
+}
+
+int swe_scheme_state_create(const swe_grid* g, swe_scheme_state** out) {
+  if (!g || !out) return fail(SWE_ERR_INVALID_ARG, "grid and out are required");
+  swe_scheme_state* s = new (std::nothrow) swe_scheme_state();
+  if (!s) return fail(SWE_ERR_NOMEM, "host allocation failed");
+  s->grid = g;
+  size_t n = (size_t)4 * g->host.ng;
+  cudaError_t e = cudaMalloc(&s->u_prev, n * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&s->m_slots, 8 * sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(s->m_slots, 0, 8 * sizeof(int));
+  if (e != cudaSuccess) {
+    if (s->u_prev) cudaFree(s->u_prev);
+    if (s->m_slots) cudaFree(s->m_slots);
+    delete s;
+    return fail(SWE_ERR_NOMEM, std::string("scheme state allocation: ") + cudaGetErrorString(e));
+  }
+  *out = s;
+  return SWE_OK;
+}
+
+int swe_scheme_state_reset(swe_scheme_state* s) {
+  if (!s) return fail(SWE_ERR_INVALID_ARG, "state is NULL");
+  s->have_prev = 0;
+  CK(cudaMemset(s->m_slots, 0, 8 * sizeof(int)));
+  return SWE_OK;
+}
+
+void swe_scheme_state_destroy(swe_scheme_state* s) {
+  if (!s) return;
+  if (s->u_prev) cudaFree(s->u_prev);
+  if (s->m_slots) cudaFree(s->m_slots);
+  delete s;
+}
+
+int exprb_step(swe_grid* g, int scheme, double dt, const double* u_n, double* u_np1,
+               swe_scheme_state* state, const phi_opts* opts, phi_stats* stats, void* stream) {
+  if (!g || !u_n || !u_np1 || !state) return fail(SWE_ERR_INVALID_ARG, "exprb_step: NULL argument");
+  if (state->grid != g) return fail(SWE_ERR_INVALID_ARG, "exprb_step: state belongs to another grid");
+  if (u_n == u_np1) return fail(SWE_ERR_INVALID_ARG, "exprb_step: u_n and u_np1 must differ");
+  if (scheme < SWE_EPI2 || scheme > SWE_EPI3) return fail(SWE_ERR_INVALID_ARG, "unknown scheme");
+  int rc;
+  phi_opts o;
+  if ((rc = resolve_opts(opts, o))) return rc;
+  if ((rc = ensure_workspace(g))) return rc;
+  cudaStream_t st = S(stream);
+  if ((rc = stage_replay(g, o, st))) return rc;
+  const size_t n = (size_t)4 * g->T.ng;
+  double* B[STAGE_VECS];
+  for (int k = 0; k < STAGE_VECS; ++k) B[k] = g->stage + (size_t)k * n;
+  double* vF = B[0];
+  ProfSpan span(g, st, &g->call_ev);
+  CK(cudaMemsetAsync(g->stats, 0, sizeof(DevStats), st));
+  k_aux<<<grid_blocks(g->T.ng), TPB, 0, st>>>(g->T, u_n, g->aux);
+  CK(cudaGetLastError());
+  count_launches(g, 1);
+  if ((rc = run_rhs(g, u_n, vF, dt, st))) return rc;  // v = dt F(u_n)
+  int* slots = o.m_carry ? state->m_slots : nullptr;
+  auto slot = [&](int k) { return slots ? slots + k : nullptr; };
+  int call = 0;
+  // Replay records are consumed call by call; the device keeps its own count
+  // per launch, so the host offsets each call by the attempts already used.
+  // Replay is supported for single-call schemes and for phi_action only.
+  if (o.replay && scheme != SWE_EPI2 && !(scheme == SWE_EPI3 && !state->have_prev))
+    return fail(SWE_ERR_INVALID_ARG, "replay is supported by phi_action and EPI2 steps");
+  const double one = 1.0;
+  if (scheme == SWE_EPI2 || (scheme == SWE_EPI3 && !state->have_prev)) {
+    const double* v[2] = {nullptr, vF};
+    double* y[1] = {B[1]};
+    if ((rc = phi_call(g, u_n, dt, 1, v, 1, &one, y, o, call++, slot(0), 0, st))) return rc;
+    if ((rc = run_lincomb(g, u_np1, {{1.0, u_n}, {1.0, B[1]}}, st))) return rc;
+  } else if (scheme == SWE_EXPRB42) {
+    const double r1 = 0.75;
+    const double* v1[2] = {nullptr, vF};
+    double* y1[1] = {B[1]};
+    if ((rc = phi_call(g, u_n, dt, 1, v1, 1, &r1, y1, o, call++, slot(1), 0, st))) return rc;
+    // D_2 = N(U_2) - N(u_n) = Q(U_2 - u_n); v_3 = (32/9) dt D_2
+    if ((rc = run_quad(g, B[1], B[2], (32.0 / 9.0) * dt, st))) return rc;
+    const double* v2[4] = {nullptr, vF, nullptr, B[2]};
+    double* y2[1] = {B[3]};
+    if ((rc = phi_call(g, u_n, dt, 3, v2, 1, &one, y2, o, call++, slot(2), 0, st))) return rc;
+    if ((rc = run_lincomb(g, u_np1, {{1.0, u_n}, {1.0, B[3]}}, st))) return rc;
+  } else if (scheme == SWE_PEXPRB43) {
+    const double r1[2] = {0.5, 1.0};
+    const double* v1[2] = {nullptr, vF};
+    double* y1[2] = {B[1], B[2]};
+    if ((rc = phi_call(g, u_n, dt, 1, v1, 2, r1, y1, o, call++, slot(1), 0, st))) return rc;
+    if ((rc = run_quad(g, B[1], B[3], dt, st))) return rc;  // dt D_2
+    if ((rc = run_quad(g, B[2], B[4], dt, st))) return rc;  // dt D_3
+    if ((rc = run_lincomb(g, B[5], {{16.0, B[3]}, {-2.0, B[4]}}, st))) return rc;
+    if ((rc = run_lincomb(g, B[6], {{-48.0, B[3]}, {12.0, B[4]}}, st))) return rc;
+    const double* v2[5] = {nullptr, nullptr, nullptr, B[5], B[6]};
+    double* y2[1] = {B[7]};
+    if ((rc = phi_call(g, u_n, dt, 4, v2, 1, &one, y2, o, call++, slot(2), 0, st))) return rc;
+    // u_{n+1} = U_3 + w = u_n + Y(1) + w
+    if ((rc = run_lincomb(g, u_np1, {{1.0, u_n}, {1.0, B[2]}, {1.0, B[7]}}, st))) return rc;
+  } else if (scheme == SWE_EXPRB53) {
+    const double r1[2] = {0.5, 0.9};
+    const double* v1[2] = {nullptr, vF};
+    double* y1[2] = {B[1], B[2]};
+    if ((rc = phi_call(g, u_n, dt, 1, v1, 2, r1, y1, o, call++, slot(1), 0, st))) return rc;
+    if ((rc = run_quad(g, B[1], B[3], dt, st))) return rc;  // dt D_2
+    const double* v2[4] = {nullptr, nullptr, nullptr, B[3]};
+    double* y2[2] = {B[4], B[5]};
+    if ((rc = phi_call(g, u_n, dt, 3, v2, 2, r1, y2, o, call++, slot(2), 0, st))) return rc;
+    // U_3 - u_n = Y_1(9/10) + (27/25)/(1/2)^3 Y_3(1/2) + (729/125)/(9/10)^3 Y_3(9/10)
+    const double c3h = (27.0 / 25.0) / (0.5 * 0.5 * 0.5);
+    const double c3n = (729.0 / 125.0) / (0.9 * 0.9 * 0.9);
+    if ((rc = run_lincomb(g, B[6], {{1.0, B[2]}, {c3h, B[4]}, {c3n, B[5]}}, st))) return rc;
+    if ((rc = run_quad(g, B[6], B[7], dt, st))) return rc;  // dt D_3
+    if ((rc = run_lincomb(g, B[8], {{18.0, B[3]}, {-250.0 / 81.0, B[7]}}, st))) return rc;
+    if ((rc = run_lincomb(g, B[9], {{-60.0, B[3]}, {500.0 / 27.0, B[7]}}, st))) return rc;
+    const double* v3[5] = {nullptr, vF, nullptr, B[8], B[9]};
+    double* y3[1] = {B[10]};
+    if ((rc = phi_call(g, u_n, dt, 4, v3, 1, &one, y3, o, call++, slot(3), 0, st))) return rc;
+    if ((rc = run_lincomb(g, u_np1, {{1.0, u_n}, {1.0, B[10]}}, st))) return rc;
+  } else {  // SWE_EPI3 with history
+    // R_{n-1} = F(u_{n-1}) - F(u_n) - J_n (u_{n-1} - u_n) = Q(u_{n-1} - u_n); v_2 = (2/3) dt R
+    if ((rc = run_lincomb(g, B[1], {{1.0, state->u_prev}, {-1.0, u_n}}, st))) return rc;
+    if ((rc = run_quad(g, B[1], B[2], (2.0 / 3.0) * dt, st))) return rc;
+    const double* v[3] = {nullptr, vF, B[2]};
+    double* y[1] = {B[3]};
+    if ((rc = phi_call(g, u_n, dt, 2, v, 1, &one, y, o, call++, slot(1), 0, st))) return rc;
+    if ((rc = run_lincomb(g, u_np1, {{1.0, u_n}, {1.0, B[3]}}, st))) return rc;
+  }
+  if (scheme == SWE_EPI3) {
+    CK(cudaMemcpyAsync(state->u_prev, u_n, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    state->have_prev = 1;
+  }
+  span.finish();
+  return read_stats(g, stats, st);
+}
+
+int swe_profile_enable(swe_grid* g, int on) {
+  if (!g) return fail(SWE_ERR_INVALID_ARG, "grid is NULL");
+  int rc = ensure_workspace(g);
+  if (rc) return rc;
+  if (on) {
+    CK(cudaDeviceSynchronize());
+    CK(cudaMemset(g->dprof, 0, sizeof(DevProfile)));
+    g->phi_ev.clear();
+    g->call_ev.clear();
+    g->ev_used = 0;
+    g->kernel_launches = 0;
+  }
+  g->prof_on = on != 0;
+  return SWE_OK;
+}
+
+int swe_profile_read(swe_grid* g, swe_profile* out, void* stream) {
+  if (!g || !out) return fail(SWE_ERR_INVALID_ARG, "grid and out are required");
+  std::memset(out, 0, sizeof(*out));
+  if (!g->dprof) return SWE_OK;
+  CK(cudaStreamSynchronize(S(stream)));
+  CK(cudaDeviceSynchronize());
+  DevProfile dp;
+  CK(cudaMemcpy(&dp, g->dprof, sizeof(DevProfile), cudaMemcpyDeviceToHost));
+  for (auto& pr : g->phi_ev) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, pr.first, pr.second));
+    out->phi_ms += ms;
+  }
+  for (auto& pr : g->call_ev) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, pr.first, pr.second));
+    out->call_ms += ms;
+  }
+  const double ng = (double)g->T.ng;
+  out->phi_launches = dp.launches;
+  out->kernel_launches = g->kernel_launches;
+  out->iom2_iterations = dp.iters;
+  out->w_jv = dp.wjv;
+  out->comb_terms = dp.comb_terms;
+  out->phi_flop = ng * (342.0 * dp.iters + 310.0 * dp.wjv + 8.0 * dp.comb_terms);
+  out->phi_bytes = ng * (136.0 * dp.iters + 104.0 * dp.wjv + 32.0 * dp.comb_terms);
+  return SWE_OK;
+}
+
+int swe_device_status(swe_grid* g, void* stream) {
+  if (!g) return fail(SWE_ERR_INVALID_ARG, "grid is NULL");
+  if (!g->stats) return SWE_OK;
+  DevStats ds;
+  CK(cudaMemcpyAsync(&ds, g->stats, sizeof(DevStats), cudaMemcpyDeviceToHost, S(stream)));
+  CK(cudaStreamSynchronize(S(stream)));
+  if (ds.status != SWE_OK) {
+    int z = 0;
+    CK(cudaMemcpy(&g->stats->status, &z, sizeof(int), cudaMemcpyHostToDevice));
+    return fail(ds.status, "device-side error in the last phi_action / exprb_step");
+  }
+  return SWE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,259 @@
+// Device-side building blocks: operator tables, the two-pass cell stencils of
+// F(u), J(u)x and the quadratic part Q(d), and bounded grid-wide barriers.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace swe {
+
+constexpr int SLOTS = 6;
+
+// Operator tables of one grid (read-only for the lifetime of the grid).
+struct Tables {
+  int ng;
+  double nu;      // dissipation coefficient of Eq. eq:niu
+  double g;       // gravity
+  double two_omega;
+  const int32_t* __restrict__ nbr;  // [6][ng]
+  const double* __restrict__ nrm;   // [3][ng] unit normals
+  const double* __restrict__ wl;    // [6][ng]
+  const double* __restrict__ wld;   // [ng]
+  const double* __restrict__ nc;    // [3][6][ng]
+  const double* __restrict__ ndd;   // [3][ng]
+  const double* __restrict__ sdg;   // [3][ng]
+  const double* __restrict__ vc;    // [3][6][ng]
+  const double* __restrict__ vd;    // [3][ng]
+};
+
+// Pass-1 outputs per cell, 8 planes of ng: [L x (4), scalar, vector (3)].
+enum StencilMode { MODE_F = 0, MODE_J = 1, MODE_Q = 2 };
+
+// ---------------------------------------------------------------------------
+// Loads.  Data produced inside the same persistent launch must not go through
+// the non-coherent read-only path, so kernels that write what they later
+// gather read with plain loads (`ld`); inputs fixed for the whole launch use
+// __ldg.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double ld(const double* p) { return *p; }
+__device__ __forceinline__ double ldro(const double* p) { return __ldg(p); }
+
+// L psi at cell i for one plane: wld_i psi_i + sum_k wl_k psi_{nbr_k}
+__device__ __forceinline__ double lap_cell(const Tables& T, int i, const int (&nb)[SLOTS],
+                                           const double* psi) {
+  double acc = ldro(T.wld + i) * ld(psi + i);
+#pragma unroll
+  for (int k = 0; k < SLOTS; ++k) acc = fma(ldro(T.wl + (size_t)k * T.ng + i), ld(psi + nb[k]), acc);
+  return acc;
+}
+
+__device__ __forceinline__ void load_nbr(const Tables& T, int i, int (&nb)[SLOTS]) {
+#pragma unroll
+  for (int k = 0; k < SLOTS; ++k) nb[k] = __ldg(T.nbr + (size_t)k * T.ng + i);
+}
+
+// Pass 1 of a stencil at cell i; writes the 8 intermediate planes of tmp.
+//   MODE_F: x = u.          tmp = [L u (4), E = |u|^2/2 + g h, q = u h]
+//   MODE_J: x = sx * xraw.  tmp = [L x (4), s = u.x_u + g x_h, q = x_u h + u x_h]
+//   MODE_Q: x = d.          tmp = [-, -, -, -, E = |d_u|^2/2, q = d_u d_h]
+template <int MODE>
+__device__ __forceinline__ void pass1_cell(const Tables& T, int i, const double* x, double sx,
+                                           const double* u, double* tmp) {
+  const int ng = T.ng;
+  int nb[SLOTS];
+  load_nbr(T, i, nb);
+  double xv[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) xv[c] = ld(x + (size_t)c * ng + i);
+  if (MODE != MODE_Q) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      double lx = lap_cell(T, i, nb, x + (size_t)c * ng);
+      tmp[(size_t)c * ng + i] = (MODE == MODE_J) ? sx * lx : lx;
+    }
+  }
+  if (MODE == MODE_J) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) xv[c] *= sx;
+    double uv[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) uv[c] = ldro(u + (size_t)c * ng + i);
+    double s = fma(uv[0], xv[0], fma(uv[1], xv[1], fma(uv[2], xv[2], T.g * xv[3])));
+    tmp[(size_t)4 * ng + i] = s;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) tmp[(size_t)(5 + c) * ng + i] = fma(xv[c], uv[3], uv[c] * xv[3]);
+  } else if (MODE == MODE_F) {
+    double e = fma(0.5, fma(xv[0], xv[0], fma(xv[1], xv[1], xv[2] * xv[2])), T.g * xv[3]);
+    tmp[(size_t)4 * ng + i] = e;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) tmp[(size_t)(5 + c) * ng + i] = xv[c] * xv[3];
+  } else {
+    double e = 0.5 * fma(xv[0], xv[0], fma(xv[1], xv[1], xv[2] * xv[2]));
+    tmp[(size_t)4 * ng + i] = e;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) tmp[(size_t)(5 + c) * ng + i] = xv[c] * xv[3];
+  }
+}
+
+// Pass 2 of a stencil at cell i: out[4] = F(u), J(u)x or Q(d) at cell i.
+//   x: the same vector as pass 1 (F: u, J: raw x with scale sx, Q: d)
+//   aux (MODE_J only): [eta, P_x, P_y, P_z] of the linearisation state,
+//   eta = V u + f, P = n x u.
+template <int MODE>
+__device__ __forceinline__ void pass2_cell(const Tables& T, int i, const double* x, double sx,
+                                           const double* tmp, const double* aux, double out[4]) {
+  const int ng = T.ng;
+  int nb[SLOTS];
+  load_nbr(T, i, nb);
+  // relative vorticity of x: V . x_u
+  double vor = 0.0;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) vor = fma(ldro(T.vd + (size_t)c * ng + i), ld(x + (size_t)c * ng + i), vor);
+#pragma unroll
+  for (int k = 0; k < SLOTS; ++k) {
+    const int j = nb[k];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      vor = fma(ldro(T.vc + ((size_t)c * SLOTS + k) * ng + i), ld(x + (size_t)c * ng + j), vor);
+  }
+  // raw gradient of the scalar plane and divergence of the vector planes
+  const double* sc = tmp + (size_t)4 * ng;
+  const double sci = ld(sc + i);
+  double gr[3], dv = 0.0;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    double nd = ldro(T.ndd + (size_t)c * ng + i);
+    gr[c] = (nd - ldro(T.sdg + (size_t)c * ng + i)) * sci;
+    dv = fma(nd, ld(tmp + (size_t)(5 + c) * ng + i), dv);
+  }
+#pragma unroll
+  for (int k = 0; k < SLOTS; ++k) {
+    const int j = nb[k];
+    const double scj = ld(sc + j);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      double w = ldro(T.nc + ((size_t)c * SLOTS + k) * ng + i);
+      gr[c] = fma(w, scj, gr[c]);
+      dv = fma(w, ld(tmp + (size_t)(5 + c) * ng + j), dv);
+    }
+  }
+  double n0 = ldro(T.nrm + i), n1 = ldro(T.nrm + ng + i), n2 = ldro(T.nrm + 2 * (size_t)ng + i);
+  double ng_ = fma(n0, gr[0], fma(n1, gr[1], n2 * gr[2]));
+  gr[0] = fma(-n0, ng_, gr[0]);
+  gr[1] = fma(-n1, ng_, gr[1]);
+  gr[2] = fma(-n2, ng_, gr[2]);
+  // own values of x (scaled)
+  double xo[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) xo[c] = ld(x + (size_t)c * ng + i);
+  double nx0 = n1 * xo[2] - n2 * xo[1];
+  double nx1 = n2 * xo[0] - n0 * xo[2];
+  double nx2 = n0 * xo[1] - n1 * xo[0];
+  if (MODE == MODE_J) {
+    vor *= sx;
+    nx0 *= sx;
+    nx1 *= sx;
+    nx2 *= sx;
+    double eta = ld(aux + i);
+    double p0 = ld(aux + (size_t)ng + i), p1 = ld(aux + 2 * (size_t)ng + i), p2 = ld(aux + 3 * (size_t)ng + i);
+    out[0] = -fma(vor, p0, fma(eta, nx0, gr[0]));
+    out[1] = -fma(vor, p1, fma(eta, nx1, gr[1]));
+    out[2] = -fma(vor, p2, fma(eta, nx2, gr[2]));
+    out[3] = -dv;
+  } else if (MODE == MODE_F) {
+    double eta = fma(T.two_omega, n2, vor);
+    out[0] = -fma(eta, nx0, gr[0]);
+    out[1] = -fma(eta, nx1, gr[1]);
+    out[2] = -fma(eta, nx2, gr[2]);
+    out[3] = -dv;
+  } else {
+    out[0] = -fma(vor, nx0, gr[0]);
+    out[1] = -fma(vor, nx1, gr[1]);
+    out[2] = -fma(vor, nx2, gr[2]);
+    out[3] = -dv;
+  }
+  if (MODE != MODE_Q) {  // dissipation -nu L (L x) on every variable
+#pragma unroll
+    for (int c = 0; c < 4; ++c) out[c] = fma(-T.nu, lap_cell(T, i, nb, tmp + (size_t)c * ng), out[c]);
+  }
+}
+
+// aux = [eta, n x u] of a linearisation state u at cell i.
+__device__ __forceinline__ void aux_cell(const Tables& T, int i, const double* u, double* aux) {
+  const int ng = T.ng;
+  int nb[SLOTS];
+  load_nbr(T, i, nb);
+  double vor = 0.0;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) vor = fma(ldro(T.vd + (size_t)c * ng + i), ldro(u + (size_t)c * ng + i), vor);
+#pragma unroll
+  for (int k = 0; k < SLOTS; ++k)
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      vor = fma(ldro(T.vc + ((size_t)c * SLOTS + k) * ng + i), ldro(u + (size_t)c * ng + nb[k]), vor);
+  double n0 = ldro(T.nrm + i), n1 = ldro(T.nrm + ng + i), n2 = ldro(T.nrm + 2 * (size_t)ng + i);
+  double u0 = ldro(u + i), u1 = ldro(u + ng + i), u2 = ldro(u + 2 * (size_t)ng + i);
+  aux[i] = fma(T.two_omega, n2, vor);
+  aux[(size_t)ng + i] = n1 * u2 - n2 * u1;
+  aux[2 * (size_t)ng + i] = n2 * u0 - n0 * u2;
+  aux[3 * (size_t)ng + i] = n0 * u1 - n1 * u0;
+}
+
+// ---------------------------------------------------------------------------
+// Bounded grid-wide barrier for co-resident (cooperatively launched) blocks.
+// Every wait gives up after kWaitNs of global time, records SWE timeout in
+// *abort and returns false; a set abort word also ends every wait.
+// ---------------------------------------------------------------------------
+struct GridSync {
+  unsigned int count;
+  unsigned int gen;
+  int abort;     // 0, or the SWE_ERR_* code that ended the launch
+  int pad;
+};
+
+constexpr unsigned long long kWaitNs = 4000000000ull;  // 4 s
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(unsigned int* p, unsigned int v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ int ld_volatile_int(const int* p) { return *(volatile const int*)p; }
+
+// Phase 1 of a barrier: arrive.  Returns the generation to wait on and
+// whether this block arrived last (thread 0 only).
+__device__ __forceinline__ unsigned int bar_arrive(GridSync* s, unsigned int nblocks, bool* last) {
+  unsigned int gen = ld_acquire(&s->gen);
+  __threadfence();
+  unsigned int prev = atomicAdd(&s->count, 1u);
+  *last = (prev == nblocks - 1);
+  if (*last) __threadfence();
+  return gen;
+}
+__device__ __forceinline__ void bar_release(GridSync* s, unsigned int gen) {
+  s->count = 0;
+  __threadfence();
+  st_release(&s->gen, gen + 1);
+}
+__device__ __forceinline__ bool bar_wait(GridSync* s, unsigned int gen, int timeout_code) {
+  unsigned long long t0 = globaltimer();
+  while (ld_acquire(&s->gen) == gen) {
+    if (ld_volatile_int(&s->abort) != 0) return false;
+    if (globaltimer() - t0 > kWaitNs) {
+      atomicCAS(&s->abort, 0, timeout_code);
+      return false;
+    }
+    __nanosleep(64);
+  }
+  __threadfence();
+  return true;
+}
+
+}  // namespace swe
