@@ -142,6 +142,20 @@ int swe_rhs(const swe_grid* grid, const double* u, double* f, void* stream);
  * device, n doubles; jx must not overlap u or x. */
 int swe_jv(const swe_grid* grid, const double* u, const double* x, double* jx, void* stream);
 
+/* jx = J(u) x like swe_jv, but without allocating any device memory.  The
+ * paper has no counterpart: this exists for callers that may not allocate at
+ * the time of the call (work enqueued during CUDA-graph stream capture, code
+ * running under another framework's memory pool or a fixed device budget,
+ * real-time loops), since swe_jv allocates the grid's workspace on first use.
+ * Scratch is a static device array in the library image sized for grids of at
+ * most 40962 cells (level 6; 3.9 MB held on every GPU that loads the
+ * library); larger grids return SWE_ERR_INVALID_ARG.  The first call on each
+ * device looks the array up (cudaGetSymbolAddress) with that device current
+ * and should come before any stream capture.  All calls share the array:
+ * calls that overlap on the GPU (e.g. on two streams) race and must be
+ * serialised by the caller.  u, x, jx: device, n doubles; jx distinct. */
+int swe_jv_noalloc(const swe_grid* grid, const double* u, const double* x, double* jx, void* stream);
+
 /* phipm_simul_iom2 (Sec. 4.3, Algorithm 1): for A = dt*J(u_lin) and vectors
  * v_0..v_p, writes y_out[i] = sum_{l=0}^{p} rho_i^l phi_l(rho_i A) v_l
  * (Eq. eq:exp_multistage with the rho^l factor the drivers of Sec. 4.4 use),

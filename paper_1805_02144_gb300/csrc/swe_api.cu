@@ -400,6 +400,16 @@ int read_stats(swe_grid* g, phi_stats* stats, cudaStream_t st) {
 
 }  // namespace
 
+// Accessors for the allocation-free entry point (swe_noalloc.cu).
+namespace swe {
+int grid_device_tables(const swe_grid* g, Tables* out) {
+  if (!g->dtab) return fail(SWE_ERR_INVALID_ARG, "grid was built on the host only");
+  *out = g->T;
+  return SWE_OK;
+}
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+}  // namespace swe
+
 // ---------------------------------------------------------------------------
 // public entry points
 // ---------------------------------------------------------------------------

@@ -1,0 +1,127 @@
+// swe_jv_noalloc: J(u) x without any device allocation.
+//
+// Who needs this: swe_jv sizes its scratch (the pass-1 planes and the
+// eta / n x u planes of the linearisation state) inside the grid's workspace,
+// which the library allocates with cudaMalloc on first use (and that workspace
+// also holds the Krylov basis of phi_action).  Some callers must not allocate
+// device memory at that point: code that enqueues work while a stream is
+// being captured into a CUDA graph (allocation is not allowed inside a
+// capture), code that runs under another framework's memory pool or a fixed
+// device-memory budget reserved at start-up, and real-time loops that cannot
+// take an allocation's latency or an out-of-memory failure mid-run.  This
+// entry point uses a scratch array that is part of the library image instead.
+//
+// The scratch is one file-scope device array of kScratchDoubles doubles
+// (12 planes of up to kMaxCells cells: 3.9 MB), resident on every GPU that
+// loads the library until the process exits.  Its device address is looked up
+// once per device with cudaGetSymbolAddress on the first call made with that
+// device current; make that first call before any stream capture begins.
+// Every call reuses the same array: each plane is fully written before it is
+// read, so nothing needs clearing, but two calls that overlap on the GPU (for
+// example on two streams) race on it and must be serialised by the caller.
+#include <cuda_runtime.h>
+
+#include <mutex>
+#include <string>
+
+#include "../../include/swe_exprb.h"
+#include "swe_dev.cuh"
+
+using namespace swe;
+
+namespace swe {
+// Device tables of a grid handle (defined with the handle in swe_api.cu).
+int grid_device_tables(const swe_grid* g, Tables* out);
+void set_last_error(const std::string& msg);
+}  // namespace swe
+
+namespace {
+
+constexpr int kMaxCells = 40962;  // level-6 grid
+constexpr size_t kScratchDoubles = (size_t)12 * kMaxCells;
+static __device__ __align__(256) double g_jv_scratch[kScratchDoubles];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+double* g_ptr[kMaxDevices] = {nullptr};
+
+__global__ void k_aux_na(Tables T, const double* __restrict__ u, double* aux) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < T.ng; i += gridDim.x * blockDim.x)
+    aux_cell(T, i, u, aux);
+}
+
+__global__ void k_pass1_na(Tables T, const double* x, const double* u, double* tmp) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < T.ng; i += gridDim.x * blockDim.x)
+    pass1_cell<MODE_J>(T, i, x, 1.0, u, tmp);
+}
+
+__global__ void k_pass2_na(Tables T, const double* x, const double* tmp, const double* aux, double* out) {
+  const int ng = T.ng;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ng; i += gridDim.x * blockDim.x) {
+    double o[4];
+    pass2_cell<MODE_J>(T, i, x, 1.0, tmp, aux, o);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) out[(size_t)c * ng + i] = o[c];
+  }
+}
+
+// Device address of the scratch array on the current device (looked up once).
+int scratch_ptr(double** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) {
+    set_last_error(std::string("swe_jv_noalloc: cudaGetDevice: ") + cudaGetErrorString(e));
+    return SWE_ERR_CUDA;
+  }
+  if (dev < 0 || dev >= kMaxDevices) {
+    set_last_error("swe_jv_noalloc: device ordinal out of range");
+    return SWE_ERR_INVALID_ARG;
+  }
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!g_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_jv_scratch);
+    if (e != cudaSuccess || !p) {
+      set_last_error(std::string("swe_jv_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+      return SWE_ERR_CUDA;
+    }
+    g_ptr[dev] = (double*)p;
+  }
+  *out = g_ptr[dev];
+  return SWE_OK;
+}
+
+}  // namespace
+
+extern "C" int swe_jv_noalloc(const swe_grid* grid, const double* u, const double* x, double* jx,
+                              void* stream) {
+  if (!grid || !u || !x || !jx) {
+    set_last_error("swe_jv_noalloc: NULL argument");
+    return SWE_ERR_INVALID_ARG;
+  }
+  Tables T;
+  int rc = grid_device_tables(grid, &T);
+  if (rc != SWE_OK) return rc;
+  if (T.ng > kMaxCells) {
+    set_last_error("swe_jv_noalloc: grid has " + std::to_string(T.ng) +
+                   " cells; the static scratch holds at most " + std::to_string(kMaxCells) +
+                   " (level 6); use swe_jv for larger grids");
+    return SWE_ERR_INVALID_ARG;
+  }
+  double* scratch = nullptr;
+  if ((rc = scratch_ptr(&scratch)) != SWE_OK) return rc;
+  double* tmp = scratch;                          // 8 planes of ng
+  double* aux = scratch + (size_t)8 * T.ng;       // 4 planes of ng
+  cudaStream_t st = (cudaStream_t)stream;
+  const int tpb = 256;
+  int nb = (T.ng + tpb - 1) / tpb;
+  k_aux_na<<<nb, tpb, 0, st>>>(T, u, aux);
+  k_pass1_na<<<nb, tpb, 0, st>>>(T, x, u, tmp);
+  k_pass2_na<<<nb, tpb, 0, st>>>(T, x, tmp, aux, jx);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_last_error(std::string("swe_jv_noalloc: launch: ") + cudaGetErrorString(e));
+    return SWE_ERR_CUDA;
+  }
+  return SWE_OK;
+}
