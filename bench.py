@@ -276,6 +276,7 @@ def gpu_arm(args) -> None:
             "hbm_gbs_algorithmic": prof["phi_bytes"] / (prof["phi_ms"] / 1e3) / 1e9,
             "hbm_frac_of_measured": (prof["phi_bytes"] / (prof["phi_ms"] / 1e3) / 1e9 / hbm) if hbm else None,
             "iom2_iterations_per_step": prof["iom2_iterations"] / args.steps,
+            "phase_ms_per_step": {k: v / args.steps for k, v in prof["phase_ms"].items()},
         },
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n},
         "gpu_launches": prof["kernel_launches"],

@@ -201,6 +201,11 @@ typedef struct {
   int64_t phi_launches;   /* persistent phi launches                         */
   int64_t kernel_launches;/* all kernels launched by the calls (phi included) */
   int64_t iom2_iterations, w_jv, comb_terms;
+  /* time of the persistent launches by phase, as seen by block 0 (work plus
+   * barrier wait): prologue, w_j pass 1, w_j pass 2, IOM2 pass 1, IOM2 pass 2
+   * (+ dots), orthogonalisation + next pass 1 (+ norm), controller tail and
+   * barrier, combination, Taylor exponential, controller head */
+  double phase_ms[10];
 } swe_profile;
 
 /* on != 0: zero the counters and start recording; on == 0: stop. */

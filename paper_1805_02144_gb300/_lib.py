@@ -49,7 +49,8 @@ class PhiStatsC(C.Structure):
 class ProfileC(C.Structure):
     _fields_ = [("phi_ms", C.c_double), ("call_ms", C.c_double), ("phi_flop", C.c_double),
                 ("phi_bytes", C.c_double), ("phi_launches", C.c_int64), ("kernel_launches", C.c_int64),
-                ("iom2_iterations", C.c_int64), ("w_jv", C.c_int64), ("comb_terms", C.c_int64)]
+                ("iom2_iterations", C.c_int64), ("w_jv", C.c_int64), ("comb_terms", C.c_int64),
+                ("phase_ms", C.c_double * 10)]
 
 
 class SweError(RuntimeError):

@@ -214,4 +214,8 @@ def swe_profile_enable(grid: Grid, on: bool = True) -> None:
 def swe_profile_read(grid: Grid, stream=None) -> dict:
     pr = _lib.ProfileC()
     check(load().swe_profile_read(grid.handle, C.byref(pr), _stream(stream)))
-    return {k: getattr(pr, k) for k, _ in _lib.ProfileC._fields_}
+    d = {k: getattr(pr, k) for k, _ in _lib.ProfileC._fields_ if k != "phase_ms"}
+    names = ["prologue", "w_pass1", "w_pass2", "iom2_pass1", "iom2_pass2_dots", "orth_pass1_norm",
+             "decide_tail", "combine", "taylor", "decide_head"]
+    d["phase_ms"] = {n: pr.phase_ms[i] for i, n in enumerate(names)}
+    return d

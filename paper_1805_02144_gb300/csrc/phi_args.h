@@ -19,6 +19,7 @@ struct DevStats {
 // Operation counters accumulated while profiling is on.
 struct DevProfile {
   long long iters, wjv, comb_terms, launches;
+  long long phase_ns[10];  // block 0's time per phase class (see phi_kernel.cu)
 };
 
 // One trace record, the same layout as the public phi_attempt.
@@ -57,7 +58,9 @@ struct PhiArgs {
   // workspace
   double* Vbuf;             // (KMAX + 1) raw basis slots of n doubles (slot 0 unused)
   double* W;                // (PMAX + 1) x n: W[0] = y_k, W[j] = w_j
-  double* tmp;              // 8 x ng pass-1 planes
+  double* tmp;              // 8 x ng pass-1 planes (Laplacian 4, scalar/vector 4)
+  double* Lring;            // 3 x n: Laplacian planes of the last three raw slots
+  double* Zbuf;             // n: A v_j before orthogonalisation
   double* part;             // nblocks x NRED partial sums
   PhiCtrl* ctrl;
   GridSync* sync;

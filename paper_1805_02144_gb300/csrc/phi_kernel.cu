@@ -25,8 +25,14 @@
 
 namespace swe {
 
-constexpr int PHI_THREADS = 256;
-constexpr double TAYLOR_THETA = 2.0;
+#ifndef PHI_MIN_BLOCKS
+#define PHI_MIN_BLOCKS 2
+#endif
+#ifndef PHI_BLOCK_THREADS
+#define PHI_BLOCK_THREADS 256
+#endif
+constexpr int PHI_THREADS = PHI_BLOCK_THREADS;
+constexpr double TAYLOR_THETA = 4.0;
 
 __device__ __forceinline__ double vld(const double* p) { return *(volatile const double*)p; }
 __device__ __forceinline__ int vldi(const int* p) { return *(volatile const int*)p; }
@@ -34,6 +40,28 @@ __device__ __forceinline__ int vldi(const int* p) { return *(volatile const int*
 struct Range {
   int c0, c1;
 };
+
+// Cells of this thread inside the block's range.  Default: block-strided.
+// SWE_WARP_CHUNKS: each warp owns a contiguous, equal share of the range (the
+// remainder spread over the warps), lanes strided inside it.
+struct CellLoop {
+  int first, end, step;
+  __device__ CellLoop(const Range& R) {
+#ifdef SWE_WARP_CHUNKS
+    const int W = PHI_THREADS / 32, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long C = R.c1 - R.c0;
+    const int ws = R.c0 + (int)(C * w / W), we = R.c0 + (int)(C * (w + 1) / W);
+    first = ws + lane;
+    end = we;
+    step = 32;
+#else
+    first = R.c0 + threadIdx.x;
+    end = R.c1;
+    step = PHI_THREADS;
+#endif
+  }
+};
+#define FOR_CELLS(i) for (int i = CL.first; i < CL.end; i += CL.step)
 
 // ---------------------------------------------------------------------------
 // block reductions in a fixed order
@@ -59,20 +87,36 @@ __device__ __forceinline__ void block_sum(double (&v)[K], double* sred) {
   __syncthreads();
 }
 
+// Phase classes timed by block 0 while profiling: time from the end of the
+// previous barrier to the end of this one (work plus wait).
+enum Phase { PH_PROLOGUE = 0, PH_W_PASS1, PH_W_PASS2, PH_K_PASS1, PH_K_PASS2, PH_ORTH, PH_DECIDE, PH_COMBINE,
+             PH_TAYLOR, PH_CONTROL };
+
 struct Shared {
+  unsigned long long t_last;
   double red[(PHI_THREADS / 32) * NRED];
   double coef[KMAX + PMAX + 4];
   int last;
   int ok;
   unsigned int gen;
   // decision scratch (block 0, warp 0)
-  double x[KMAX + PMAX + 8], y[KMAX + PMAX + 8], acc[KMAX + PMAX + 8];
+  double x[KMAX + PMAX + 8], y[KMAX + PMAX + 8];
+  double ck[40];
   double hd[KMAX + 1], hu[KMAX + 1], hl[KMAX + 2];
+  double scal[4];
 };
+
+__device__ __forceinline__ void phase_tick(const PhiArgs& a, Shared& sh, int phase) {
+  if (a.prof && blockIdx.x == 0 && threadIdx.x == 0) {
+    unsigned long long now = globaltimer();
+    a.prof->phase_ns[phase] += (long long)(now - sh.t_last);
+    sh.t_last = now;
+  }
+}
 
 // Plain grid barrier.  Returns false (uniformly per block) when the launch is
 // being aborted.
-__device__ bool grid_barrier(const PhiArgs& a, Shared& sh) {
+__device__ bool grid_barrier(const PhiArgs& a, Shared& sh, int phase) {
   __syncthreads();
   if (threadIdx.x == 0) {
     bool last;
@@ -83,6 +127,7 @@ __device__ bool grid_barrier(const PhiArgs& a, Shared& sh) {
     else
       ok = bar_wait(a.sync, gen, SWE_ERR_TIMEOUT);
     sh.ok = ok && (ld_volatile_int(&a.sync->abort) == 0);
+    phase_tick(a, sh, phase);
   }
   __syncthreads();
   return sh.ok;
@@ -92,7 +137,7 @@ __device__ bool grid_barrier(const PhiArgs& a, Shared& sh) {
 // to arrive sums the block partials in block order, stores them in
 // ctrl->red[], runs post(ctrl) on its thread 0, and releases the barrier.
 template <int K, class Post>
-__device__ bool grid_reduce(const PhiArgs& a, Shared& sh, double (&v)[K], Post post) {
+__device__ bool grid_reduce(const PhiArgs& a, Shared& sh, double (&v)[K], int phase, Post post) {
   block_sum<K>(v, sh.red);
   if (threadIdx.x == 0) {
     for (int k = 0; k < K; ++k) a.part[(size_t)blockIdx.x * NRED + k] = v[k];
@@ -121,6 +166,7 @@ __device__ bool grid_reduce(const PhiArgs& a, Shared& sh, double (&v)[K], Post p
     bool ok = bar_wait(a.sync, sh.gen, SWE_ERR_TIMEOUT);
     sh.ok = ok && (ld_volatile_int(&a.sync->abort) == 0);
   }
+  if (threadIdx.x == 0) phase_tick(a, sh, phase);
   __syncthreads();
   return sh.ok;
 }
@@ -135,76 +181,69 @@ __device__ __forceinline__ double* raw_slot(const PhiArgs& a, int j) {
 }
 
 // ---------------------------------------------------------------------------
-// Augmented exponential by scaled Taylor series (one warp).
-// Hhat (size M = m+p+1): Hhat[0:m,0:m] = tau H_m (tridiagonal), Hhat[0,m] = 1,
-// Hhat[m+k, m+k+1] = 1 (k < p).  The last column of exp(Hhat) holds
-// phi_{p+1}(tau H) e_1 in its first m rows.  exp(Hhat) e_{M-1} =
-// (exp(Hhat/s))^s e_{M-1}, each factor a Taylor series summed until two
-// consecutive terms are below the double-precision unit roundoff relative to
-// the sum, with s = ceil(||Hhat||_1 / 2).
+// Augmented exponential by scaled Taylor series (all threads of block 0, one
+// row per thread).  Hhat (size M = m+p+1): Hhat[0:m,0:m] = tau H_m
+// (tridiagonal), Hhat[0,m] = 1, Hhat[m+k, m+k+1] = 1 (k < p).  The last column
+// of exp(Hhat) holds phi_{p+1}(tau H) e_1 in its first m rows:
+// exp(Hhat) e_{M-1} = (exp(Hhat/s))^s e_{M-1}, s = ceil(||Hhat||_1 / THETA),
+// each factor the Taylor polynomial of degree TAYLOR_TERMS.  With
+// ||Hhat/s||_1 <= 4 the truncated tail is below 4^33/33! < 1e-17 of the
+// vector, so a fixed degree needs no per-term convergence test.
+// On return sh.x[0:m] = phi_{p+1}(tau H) e_1 and sh.y[0:m] = phi_p(tau H) e_1.
 // ---------------------------------------------------------------------------
+constexpr int TAYLOR_TERMS = 32;
+
 __device__ void taylor_phi(Shared& sh, int m, int p, double tau, double hnorm) {
-  const int lane = threadIdx.x;
+  const int r = threadIdx.x;
   const int M = m + p + 1;
   const int s = (int)fmax(1.0, ceil(hnorm / TAYLOR_THETA));
-  const double inv_s = 1.0 / (double)s;
-  for (int r = lane; r < M; r += 32) sh.x[r] = (r == M - 1) ? 1.0 : 0.0;
-  __syncwarp();
-  for (int step = 0; step < s; ++step) {
-    for (int r = lane; r < M; r += 32) sh.acc[r] = sh.x[r];
-    __syncwarp();
-    double prev = INFINITY;
-    for (int k = 1; k <= 60; ++k) {
-      // y = (Hhat/s) x / k, written back into x
-      for (int r = lane; r < M; r += 32) {
-        double v;
-        if (r < m) {
-          v = sh.hd[r] * sh.x[r];
-          if (r > 0) v = fma(sh.hl[r], sh.x[r - 1], v);
-          if (r < m - 1) v = fma(sh.hu[r], sh.x[r + 1], v);
-          v *= tau;
-          if (r == 0) v += sh.x[m];
-        } else if (r < m + p) {
-          v = sh.x[r + 1];
-        } else {
-          v = 0.0;
-        }
-        sh.y[r] = v * (inv_s / (double)k);
-      }
-      __syncwarp();
-      double tn = 0.0, an = 0.0;
-      for (int r = lane; r < M; r += 32) {
-        double tv = sh.y[r];
-        sh.x[r] = tv;
-        double av = sh.acc[r] + tv;
-        sh.acc[r] = av;
-        tn = fmax(tn, fabs(tv));
-        an = fmax(an, fabs(av));
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        tn = fmax(tn, __shfl_xor_sync(0xffffffffu, tn, o));
-        an = fmax(an, __shfl_xor_sync(0xffffffffu, an, o));
-      }
-      __syncwarp();
-      if (tn + prev <= 1.1102230246251565e-16 * an) break;
-      prev = tn;
-    }
-    for (int r = lane; r < M; r += 32) sh.x[r] = sh.acc[r];
-    __syncwarp();
+  // row r of (tau H): coefficients held in registers
+  double cd = 0.0, cl = 0.0, cu = 0.0;
+  if (r < m) {
+    cd = tau * sh.hd[r];
+    if (r > 0) cl = tau * sh.hl[r];
+    if (r < m - 1) cu = tau * sh.hu[r];
   }
-  // sh.x[0:m] = phi_{p+1}(tau H) e_1;  phi_p(tau H) e_1 = tau H phi_{p+1} + e_1/p!  (Eq. eq3.7)
-  double fact = 1.0;
-  for (int k = 2; k <= p; ++k) fact *= k;
-  for (int r = lane; r < m; r += 32) {
-    double v = sh.hd[r] * sh.x[r];
-    if (r > 0) v = fma(sh.hl[r], sh.x[r - 1], v);
-    if (r < m - 1) v = fma(sh.hu[r], sh.x[r + 1], v);
-    v *= tau;
-    if (r == 0) v += 1.0 / fact;
+  if (r >= 1 && r <= TAYLOR_TERMS) sh.ck[r] = 1.0 / ((double)s * (double)r);
+  double acc = (r == M - 1) ? 1.0 : 0.0;
+  if (r < M) sh.x[r] = acc;
+  __syncthreads();
+  for (int step = 0; step < s; ++step) {
+    // sh.x holds the current term (starting with the vector itself)
+    for (int k = 1; k <= TAYLOR_TERMS; ++k) {
+      double v = 0.0;
+      if (r < m) {
+        v = cd * sh.x[r];
+        if (r > 0) v = fma(cl, sh.x[r - 1], v);
+        if (r < m - 1) v = fma(cu, sh.x[r + 1], v);
+        if (r == 0) v += sh.x[m];
+        v *= sh.ck[k];
+      } else if (r < m + p) {
+        v = sh.x[r + 1] * sh.ck[k];
+      }
+      __syncthreads();
+      if (r < M) {
+        sh.x[r] = v;
+        acc += v;
+      }
+      __syncthreads();
+    }
+    if (r < M) sh.x[r] = acc;
+    __syncthreads();
+  }
+  // phi_p(tau H) e_1 = tau H phi_{p+1}(tau H) e_1 + e_1 / p!   (Eq. eq3.7)
+  if (r < m) {
+    double v = cd * sh.x[r];
+    if (r > 0) v = fma(cl, sh.x[r - 1], v);
+    if (r < m - 1) v = fma(cu, sh.x[r + 1], v);
+    if (r == 0) {
+      double fact = 1.0;
+      for (int k = 2; k <= p; ++k) fact *= k;
+      v += 1.0 / fact;
+    }
     sh.y[r] = v;
   }
-  __syncwarp();
+  __syncthreads();
 }
 
 __device__ __forceinline__ long long nint_d(double x) { return (long long)floor(x + 0.5); }
@@ -223,7 +262,8 @@ __device__ double cost_fn(double tau, int m, int p, double remaining, double N, 
 }
 
 // Error estimate, acceptance test and controller (Algorithm 1 steps 2(ii)-6),
-// executed by warp 0 of block 0.  Writes the decision into ctrl.
+// executed by all threads of block 0 (uniform control flow; the scalar
+// controller runs on thread 0).  Writes the decision into ctrl.
 __device__ void decide(const PhiArgs& a, Shared& sh) {
   volatile PhiCtrl* C = a.ctrl;
   const int lane = threadIdx.x;
@@ -258,23 +298,27 @@ __device__ void decide(const PhiArgs& a, Shared& sh) {
   double eps = 0.0, hnorm = 1.0, hnext = 0.0;
   if (beta > 0.0) {
     m_use = min(m, (int)C->size);
-    for (int r = lane; r <= m_use; r += 32) {
+    for (int r = lane; r <= m_use; r += PHI_THREADS) {
       sh.hd[r] = C->hd[r];
       sh.hu[r] = C->hu[r];
       sh.hl[r] = C->hl[r];
     }
-    __syncwarp();
-    double cs = 0.0;
-    for (int j = lane; j < m_use; j += 32) {
-      double s = fabs(sh.hd[j]);
-      if (j > 0) s += fabs(sh.hu[j - 1]);
-      if (j + 1 < m_use) s += fabs(sh.hl[j + 1]);
-      cs = fmax(cs, s);
+    __syncthreads();
+    if (lane == 0) {
+      double cs = 0.0;
+      for (int j = 0; j < m_use; ++j) {
+        double s = fabs(sh.hd[j]);
+        if (j > 0) s += fabs(sh.hu[j - 1]);
+        if (j + 1 < m_use) s += fabs(sh.hl[j + 1]);
+        cs = fmax(cs, s);
+      }
+      sh.scal[0] = cs;
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) cs = fmax(cs, __shfl_xor_sync(0xffffffffu, cs, o));
-    hnorm = fmax(tau_k * cs, 1.0);
+    __syncthreads();
+    hnorm = fmax(tau_k * sh.scal[0], 1.0);
+    phase_tick(a, sh, PH_CONTROL);
     taylor_phi(sh, m_use, p, tau_k, hnorm);
+    phase_tick(a, sh, PH_TAYLOR);
     hnext = (C->broken && m_use == C->size) ? 0.0 : sh.hl[m_use];
     eps = pow(tau_k, (double)p) * beta * tau_k * fabs(hnext) * fabs(sh.x[m_use - 1]);
   }
@@ -285,12 +329,12 @@ __device__ void decide(const PhiArgs& a, Shared& sh) {
   if (accepted) {
     const double tp = pow(tau_k, (double)p);
     if (beta > 0.0) {
-      for (int r = lane; r < m_use; r += 32) C->cV[r] = tp * beta * sh.y[r] * C->sig[r];
+      for (int r = lane; r < m_use; r += PHI_THREADS) C->cV[r] = tp * beta * sh.y[r] * C->sig[r];
       if (lane == 0)
         C->cV[m_use] = hnext != 0.0 ? tp * beta * tau_k * hnext * sh.x[m_use - 1] * C->sig[m_use] : 0.0;
     }
   }
-  __syncwarp();
+  __syncthreads();
   if (lane != 0) return;
 
   // proposals (reading R8 of the oracle, the same arithmetic)
@@ -390,7 +434,7 @@ __device__ void decide(const PhiArgs& a, Shared& sh) {
 // ---------------------------------------------------------------------------
 // the kernel
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(PHI_THREADS, 2) phi_kernel(const __grid_constant__ PhiArgs a) {
+__global__ void __launch_bounds__(PHI_THREADS, PHI_MIN_BLOCKS) phi_kernel(const __grid_constant__ PhiArgs a) {
   __shared__ Shared sh;
   const Tables& T = a.T;
   const int ng = T.ng;
@@ -398,9 +442,11 @@ __global__ void __launch_bounds__(PHI_THREADS, 2) phi_kernel(const __grid_consta
   const int p = a.p;
   const int chunk = (ng + gridDim.x - 1) / gridDim.x;
   const Range R{min(ng, (int)blockIdx.x * chunk), min(ng, ((int)blockIdx.x + 1) * chunk)};
+  const CellLoop CL(R);
   PhiCtrl* C = a.ctrl;
 
   // ---- prologue: y = v_0, norms of the inputs -----------------------------
+  if (threadIdx.x == 0) sh.t_last = globaltimer();
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     C->status = SWE_OK;
     C->n_jv = C->n_sub = C->n_rej = C->m_last = C->m_max_used = 0;
@@ -413,7 +459,7 @@ __global__ void __launch_bounds__(PHI_THREADS, 2) phi_kernel(const __grid_consta
     double v[NRED];
 #pragma unroll
     for (int k = 0; k < NRED; ++k) v[k] = 0.0;
-    for (int i = R.c0 + threadIdx.x; i < R.c1; i += PHI_THREADS) {
+    FOR_CELLS(i) {
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
         const size_t e = (size_t)c * ng + i;
@@ -442,11 +488,11 @@ __global__ void __launch_bounds__(PHI_THREADS, 2) phi_kernel(const __grid_consta
       c->done = (scale == 0.0) || !isfinite(scale);
       if (!isfinite(scale)) c->status = SWE_ERR_NONFINITE;
     };
-    if (!grid_reduce<NRED>(a, sh, v, post)) goto finish;
+    if (!grid_reduce<NRED>(a, sh, v, PH_PROLOGUE, post)) goto finish;
   }
   if (vldi(&C->done)) {
     for (int o = 0; o < a.ns; ++o)
-      for (int i = R.c0 + threadIdx.x; i < R.c1; i += PHI_THREADS)
+      FOR_CELLS(i)
         for (int c = 0; c < 4; ++c) a.y_out[o][(size_t)c * ng + i] = 0.0;
     goto finish;
   }
@@ -473,14 +519,14 @@ __global__ void __launch_bounds__(PHI_THREADS, 2) phi_kernel(const __grid_consta
         double* wprev = a.W + (size_t)(j - 1) * n;
         double* wj = a.W + (size_t)j * n;
         if (nz_prev) {
-          for (int i = R.c0 + threadIdx.x; i < R.c1; i += PHI_THREADS)
-            pass1_cell<MODE_J>(T, i, wprev, 1.0, a.u_lin, a.tmp);
-          if (!grid_barrier(a, sh)) goto finish;
+          FOR_CELLS(i)
+            pass1_cell<MODE_J>(T, i, wprev, 1.0, a.u_lin, a.tmp, a.tmp + (size_t)4 * ng);
+          if (!grid_barrier(a, sh, PH_W_PASS1)) goto finish;
         }
         double v[2] = {0.0, 0.0};
-        for (int i = R.c0 + threadIdx.x; i < R.c1; i += PHI_THREADS) {
+        FOR_CELLS(i) {
           double o[4] = {0.0, 0.0, 0.0, 0.0};
-          if (nz_prev) pass2_cell<MODE_J>(T, i, wprev, 1.0, a.tmp, a.aux, o);
+          if (nz_prev) pass2_cell<MODE_J>(T, i, wprev, 1.0, a.tmp, a.tmp + (size_t)4 * ng, a.aux, o);
 #pragma unroll
           for (int c = 0; c < 4; ++c) {
             const size_t e = (size_t)c * ng + i;
@@ -511,7 +557,7 @@ __global__ void __launch_bounds__(PHI_THREADS, 2) phi_kernel(const __grid_consta
             }
           }
         };
-        if (!grid_reduce<2>(a, sh, v, post)) goto finish;
+        if (!grid_reduce<2>(a, sh, v, PH_W_PASS2, post)) goto finish;
       }
 
       // ---- attempts on this substep ---------------------------------------
@@ -527,24 +573,35 @@ __global__ void __launch_bounds__(PHI_THREADS, 2) phi_kernel(const __grid_consta
           }
           m_req = min(m_req, KMAX);
           // ---- IOM2: extend the basis to m_req columns (step 2(i)) --------
+          // Per column j: pass 2 (z = A v_j and the two window dots) and the
+          // fused orthogonalisation + pass 1 of the next vector, each ended
+          // by one grid reduction.  Pass-1 planes of raw slot j: Laplacian in
+          // Lring[j % 3], scalar/vector planes in SQ.
+          double* SQ = a.tmp + (size_t)4 * ng;
           while (vldi(&C->size) < m_req && !vldi(&C->broken)) {
             const int j = vldi(&C->size);
             double* rj = raw_slot(a, j);
             double* rj1 = raw_slot(a, j + 1);
             double* rjm = j > 0 ? raw_slot(a, j - 1) : nullptr;
+            double* Lj = a.Lring + (size_t)(j % 3) * n;
+            double* Ljm = a.Lring + (size_t)((j + 2) % 3) * n;
+            double* Lj1 = a.Lring + (size_t)((j + 1) % 3) * n;
             const double sj = vld(&C->sig[j]);
-            for (int i = R.c0 + threadIdx.x; i < R.c1; i += PHI_THREADS)
-              pass1_cell<MODE_J>(T, i, rj, sj, a.u_lin, a.tmp);
-            if (!grid_barrier(a, sh)) goto finish;
+            if (j == 0) {
+              FOR_CELLS(i)
+                pass1_cell<MODE_J>(T, i, rj, 1.0, a.u_lin, Lj, SQ);
+              if (!grid_barrier(a, sh, PH_K_PASS1)) goto finish;
+            }
+            const double zs = a.dt * sj;
             double v[2] = {0.0, 0.0};
-            for (int i = R.c0 + threadIdx.x; i < R.c1; i += PHI_THREADS) {
+            FOR_CELLS(i) {
               double o[4];
-              pass2_cell<MODE_J>(T, i, rj, sj, a.tmp, a.aux, o);
+              pass2_cell<MODE_J>(T, i, rj, 1.0, Lj, SQ, a.aux, o);
 #pragma unroll
               for (int c = 0; c < 4; ++c) {
                 const size_t e = (size_t)c * ng + i;
-                double z = a.dt * o[c];
-                rj1[e] = z;
+                double z = zs * o[c];
+                a.Zbuf[e] = z;
                 if (rjm) v[0] = fma(z, rjm[e], v[0]);
                 v[1] = fma(z, rj[e], v[1]);
               }
@@ -553,21 +610,13 @@ __global__ void __launch_bounds__(PHI_THREADS, 2) phi_kernel(const __grid_consta
               if (j > 0) c->hu[j - 1] = c->sig[j - 1] * c->red[0];
               c->hd[j] = c->sig[j] * c->red[1];
             };
-            if (!grid_reduce<2>(a, sh, v, post_dots)) goto finish;
-            // z <- z - h_{j-1,j} v_{j-1} - h_{j,j} v_j, and its norm
-            const double cm = j > 0 ? vld(&C->hu[j - 1]) * vld(&C->sig[j - 1]) : 0.0;
-            const double cj = vld(&C->hd[j]) * sj;
+            if (!grid_reduce<2>(a, sh, v, PH_K_PASS2, post_dots)) goto finish;
+            // z' = z - h_{j-1,j} v_{j-1} - h_{j,j} v_j with its pass-1 planes
+            const double am = j > 0 ? vld(&C->hu[j - 1]) * vld(&C->sig[j - 1]) : 0.0;
+            const double aj = vld(&C->hd[j]) * sj;
             double w[1] = {0.0};
-            for (int i = R.c0 + threadIdx.x; i < R.c1; i += PHI_THREADS) {
-#pragma unroll
-              for (int c = 0; c < 4; ++c) {
-                const size_t e = (size_t)c * ng + i;
-                double z = fma(-cj, rj[e], rj1[e]);
-                if (rjm) z = fma(-cm, rjm[e], z);
-                rj1[e] = z;
-                w[0] = fma(z, z, w[0]);
-              }
-            }
+            FOR_CELLS(i)
+              w[0] += orth_pass1_cell(T, i, a.Zbuf, rj, rjm, aj, am, Lj, Ljm, rj1, Lj1, a.u_lin, SQ);
             GridSync* gs = a.sync;
             auto post_norm = [gs, j](volatile PhiCtrl* c) {
               double hn = sqrt((double)c->red[0]);
@@ -589,12 +638,12 @@ __global__ void __launch_bounds__(PHI_THREADS, 2) phi_kernel(const __grid_consta
                 c->sig[j + 1] = 1.0 / hn;
               }
             };
-            if (!grid_reduce<1>(a, sh, w, post_norm)) goto finish;
+            if (!grid_reduce<1>(a, sh, w, PH_ORTH, post_norm)) goto finish;
           }
         }
         // ---- exponential, error estimate, controller (steps 2(ii)-6) -------
-        if (blockIdx.x == 0 && threadIdx.x < 32) decide(a, sh);
-        if (!grid_barrier(a, sh)) goto finish;
+        if (blockIdx.x == 0) decide(a, sh);
+        if (!grid_barrier(a, sh, PH_DECIDE)) goto finish;
         if (!vldi(&C->accept)) continue;
 
         // ---- y_{k+1} = tau^p phi_p(tau A) w_p + sum_{j<p} tau^j/j! w_j (eq3.17)
@@ -605,7 +654,7 @@ __global__ void __launch_bounds__(PHI_THREADS, 2) phi_kernel(const __grid_consta
         const bool land = vldi(&C->land) != 0;
         double* yo = land ? a.y_out[oi] : nullptr;
         double v[1] = {0.0};
-        for (int i = R.c0 + threadIdx.x; i < R.c1; i += PHI_THREADS) {
+        FOR_CELLS(i) {
 #pragma unroll
           for (int c = 0; c < 4; ++c) {
             const size_t e = (size_t)c * ng + i;
@@ -618,7 +667,7 @@ __global__ void __launch_bounds__(PHI_THREADS, 2) phi_kernel(const __grid_consta
           }
         }
         auto post_y = [](volatile PhiCtrl* c) { c->wnz[0] = c->red[0] > 0.0; };
-        if (!grid_reduce<1>(a, sh, v, post_y)) goto finish;
+        if (!grid_reduce<1>(a, sh, v, PH_COMBINE, post_y)) goto finish;
         break;
       }
     }
@@ -646,10 +695,33 @@ finish:
   }
 }
 
-int launch_phi_kernel(const PhiArgs& a, int nblocks, cudaStream_t stream) {
-  void* args[] = {(void*)&a};
-  cudaError_t e = cudaLaunchCooperativeKernel((void*)phi_kernel, dim3(nblocks), dim3(PHI_THREADS),
-                                              args, 0, stream);
+// Cooperative launch (all blocks co-resident: the grid barriers need it).
+// With a non-empty table window the operator tables get a persisting L2
+// access policy for this launch, so they stay cached next to the vectors.
+int launch_phi_kernel(const PhiArgs& a, int nblocks, cudaStream_t stream, const void* tab_base,
+                      size_t tab_bytes) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(nblocks);
+  cfg.blockDim = dim3(PHI_THREADS);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[2];
+  int na = 0;
+  attr[na].id = cudaLaunchAttributeCooperative;
+  attr[na].val.cooperative = 1;
+  ++na;
+  if (tab_base && tab_bytes > 0) {
+    attr[na].id = cudaLaunchAttributeAccessPolicyWindow;
+    attr[na].val.accessPolicyWindow.base_ptr = const_cast<void*>(tab_base);
+    attr[na].val.accessPolicyWindow.num_bytes = tab_bytes;
+    attr[na].val.accessPolicyWindow.hitRatio = 1.0f;
+    attr[na].val.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+    attr[na].val.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+    ++na;
+  }
+  cfg.attrs = attr;
+  cfg.numAttrs = na;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, phi_kernel, a);
   return e == cudaSuccess ? 0 : (int)e;
 }
 

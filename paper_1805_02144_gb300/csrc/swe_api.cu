@@ -15,7 +15,8 @@
 #include "swe_dev.cuh"
 
 namespace swe {
-int launch_phi_kernel(const PhiArgs& a, int nblocks, cudaStream_t stream);
+int launch_phi_kernel(const PhiArgs& a, int nblocks, cudaStream_t stream, const void* tab_base,
+                      size_t tab_bytes);
 int phi_kernel_max_blocks(int* nblocks);
 }  // namespace swe
 
@@ -58,6 +59,8 @@ struct swe_grid {
   double* W = nullptr;
   double* tmp = nullptr;
   double* tmp2 = nullptr;
+  double* Lring = nullptr;
+  double* Zbuf = nullptr;
   double* aux = nullptr;
   double* part = nullptr;
   double* stage = nullptr;   // STAGE_VECS vectors of n
@@ -68,6 +71,8 @@ struct swe_grid {
   double* replay = nullptr;
   int replay_cap = 0;
   int nblocks = 0;
+  size_t tab_bytes = 0;      // size of the table allocation
+  size_t l2_window = 0;      // persisting-L2 window over the tables (0: none)
   // profiling (swe_profile_enable)
   bool prof_on = false;
   DevProfile* dprof = nullptr;
@@ -99,7 +104,7 @@ __global__ void k_aux(Tables T, const double* __restrict__ u, double* aux) {
 template <int MODE>
 __global__ void k_pass1(Tables T, const double* x, double sx, const double* u, double* tmp) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < T.ng; i += gridDim.x * blockDim.x)
-    pass1_cell<MODE>(T, i, x, sx, u, tmp);
+    pass1_cell<MODE>(T, i, x, sx, u, tmp, tmp + (size_t)4 * T.ng);
 }
 
 // out = alpha * stencil(x)  (+ beta_ * add, when add != nullptr)
@@ -109,7 +114,7 @@ __global__ void k_pass2(Tables T, const double* x, double sx, const double* tmp,
   const int ng = T.ng;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ng; i += gridDim.x * blockDim.x) {
     double o[4];
-    pass2_cell<MODE>(T, i, x, sx, tmp, aux, o);
+    pass2_cell<MODE>(T, i, x, sx, tmp, tmp + (size_t)4 * ng, aux, o);
 #pragma unroll
     for (int c = 0; c < 4; ++c) out[(size_t)c * ng + i] = alpha * o[c];
   }
@@ -222,16 +227,21 @@ int upload_grid(swe_grid* g) {
   const int32_t* d_nbr = nullptr;
   const double *d_nrm = nullptr, *d_wl = nullptr, *d_wld = nullptr, *d_nc = nullptr, *d_ndd = nullptr,
                *d_sdg = nullptr, *d_vc = nullptr, *d_vd = nullptr;
+  // the kernels read the G diagonal ndd - sdg directly (table "sdg" of the
+  // device copy holds that difference)
+  std::vector<double> gdg(h.sdg.size());
+  for (size_t k = 0; k < gdg.size(); ++k) gdg[k] = h.ndd[k] - h.sdg[k];
   Part parts[] = {
       {h.nbr.data(), h.nbr.size() * 4, (void**)&d_nbr},  {h.xyz.data(), h.xyz.size() * 8, (void**)&d_nrm},
       {h.wl.data(), h.wl.size() * 8, (void**)&d_wl},     {h.wld.data(), h.wld.size() * 8, (void**)&d_wld},
       {h.nc.data(), h.nc.size() * 8, (void**)&d_nc},     {h.ndd.data(), h.ndd.size() * 8, (void**)&d_ndd},
-      {h.sdg.data(), h.sdg.size() * 8, (void**)&d_sdg},  {h.vc.data(), h.vc.size() * 8, (void**)&d_vc},
+      {gdg.data(), gdg.size() * 8, (void**)&d_sdg},  {h.vc.data(), h.vc.size() * 8, (void**)&d_vc},
       {h.vd.data(), h.vd.size() * 8, (void**)&d_vd},
   };
   size_t total = 0;
   for (auto& p : parts) total += (p.bytes + 255) & ~size_t(255);
   CK(cudaMalloc(&g->dtab, total));
+  g->tab_bytes = total;
   size_t off = 0;
   for (auto& p : parts) {
     char* dst = (char*)g->dtab + off;
@@ -247,7 +257,7 @@ int upload_grid(swe_grid* g) {
   T.wld = d_wld;
   T.nc = d_nc;
   T.ndd = d_ndd;
-  T.sdg = d_sdg;
+  T.gdg = d_sdg;
   T.vc = d_vc;
   T.vd = d_vd;
   return SWE_OK;
@@ -265,6 +275,8 @@ int ensure_workspace(swe_grid* g) {
       (size_t)(PMAX + 1) * n * 8,  // W
       8 * ng * 8,                  // tmp
       8 * ng * 8,                  // tmp2
+      3 * n * 8,                   // Lring
+      n * 8,                       // Zbuf
       4 * ng * 8,                  // aux
       (size_t)nb * NRED * 8,       // part
       (size_t)STAGE_VECS * n * 8,  // stage
@@ -278,15 +290,33 @@ int ensure_workspace(swe_grid* g) {
     return fail(SWE_ERR_NOMEM, std::string("workspace allocation failed: ") + cudaGetErrorString(e));
   }
   char* p = (char*)g->dws;
-  void** dst[] = {(void**)&g->Vbuf, (void**)&g->W,     (void**)&g->tmp,   (void**)&g->tmp2,
-                  (void**)&g->aux,  (void**)&g->part,  (void**)&g->stage, (void**)&g->ctrl,
-                  (void**)&g->sync, (void**)&g->stats, (void**)&g->trace, (void**)&g->dprof};
-  for (int k = 0; k < 12; ++k) {
+  void** dst[] = {(void**)&g->Vbuf,  (void**)&g->W,     (void**)&g->tmp,   (void**)&g->tmp2,
+                  (void**)&g->Lring, (void**)&g->Zbuf,  (void**)&g->aux,   (void**)&g->part,
+                  (void**)&g->stage, (void**)&g->ctrl,  (void**)&g->sync,  (void**)&g->stats,
+                  (void**)&g->trace, (void**)&g->dprof};
+  static_assert(sizeof(sizes) / sizeof(sizes[0]) == 14, "workspace layout");
+  for (int k = 0; k < 14; ++k) {
     *dst[k] = p;
     p += (sizes[k] + 255) & ~size_t(255);
   }
   g->ws_bytes = total;
   CK(cudaMemset(g->dws, 0, total));
+#ifdef SWE_L2_PERSIST
+  {
+    // Reserve persisting L2 for the operator tables (a limit of this
+    // process's context, released with it) and window the persistent launch.
+    int dev = 0, max_persist = 0, max_window = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, dev);
+    cudaDeviceGetAttribute(&max_window, cudaDevAttrMaxAccessPolicyWindowSize, dev);
+    size_t want = g->tab_bytes;
+    if (want > (size_t)max_persist) want = (size_t)max_persist;
+    if (want > (size_t)max_window) want = (size_t)max_window;
+    if (want > 0 && cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want) == cudaSuccess)
+      g->l2_window = want;
+    cudaGetLastError();
+  }
+#endif
   return SWE_OK;
 }
 
@@ -333,6 +363,8 @@ int phi_call(swe_grid* g, const double* u_lin, double dt, int p, const double* c
   a.Vbuf = g->Vbuf;
   a.W = g->W;
   a.tmp = g->tmp;
+  a.Lring = g->Lring;
+  a.Zbuf = g->Zbuf;
   a.part = g->part;
   a.ctrl = g->ctrl;
   a.sync = g->sync;
@@ -355,7 +387,7 @@ int phi_call(swe_grid* g, const double* u_lin, double dt, int p, const double* c
   a.prof = g->prof_on ? g->dprof : nullptr;
   CK(cudaMemsetAsync(g->sync, 0, sizeof(GridSync), st));
   ProfSpan span(g, st, &g->phi_ev);
-  int e = launch_phi_kernel(a, g->nblocks, st);
+  int e = launch_phi_kernel(a, g->nblocks, st, g->l2_window ? g->dtab : nullptr, g->l2_window);
   if (e != 0) return cuda_fail((cudaError_t)e, "cudaLaunchCooperativeKernel(phi_kernel)");
   span.finish();
   count_launches(g, 1);
@@ -746,6 +778,7 @@ int swe_profile_read(swe_grid* g, swe_profile* out, void* stream) {
   out->comb_terms = dp.comb_terms;
   out->phi_flop = ng * (342.0 * dp.iters + 310.0 * dp.wjv + 8.0 * dp.comb_terms);
   out->phi_bytes = ng * (136.0 * dp.iters + 104.0 * dp.wjv + 32.0 * dp.comb_terms);
+  for (int k = 0; k < 10; ++k) out->phase_ms[k] = 1e-6 * (double)dp.phase_ns[k];
   return SWE_OK;
 }
 

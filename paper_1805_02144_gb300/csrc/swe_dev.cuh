@@ -20,7 +20,7 @@ struct Tables {
   const double* __restrict__ wld;   // [ng]
   const double* __restrict__ nc;    // [3][6][ng]
   const double* __restrict__ ndd;   // [3][ng]
-  const double* __restrict__ sdg;   // [3][ng]
+  const double* __restrict__ gdg;   // [3][ng] G diagonal (ndd - sdg of the host tables)
   const double* __restrict__ vc;    // [3][6][ng]
   const double* __restrict__ vd;    // [3][ng]
 };
@@ -36,28 +36,68 @@ enum StencilMode { MODE_F = 0, MODE_J = 1, MODE_Q = 2 };
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double ld(const double* p) { return *p; }
 __device__ __forceinline__ double ldro(const double* p) { return __ldg(p); }
+// Operator tables are read once per cell and pass: with SWE_TABLE_NOALLOC they
+// bypass L1 allocation so that L1 keeps the gathered vectors.
+// With SWE_TABLE_EVICT_FIRST they are also marked first to leave L2, so the
+// gathered vectors (written one phase earlier) stay L2-resident.
+#if defined(SWE_TABLE_EVICT_FIRST)
+__device__ __forceinline__ unsigned long long l2_evict_first_policy() {
+  unsigned long long pol;
+  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+#endif
+__device__ __forceinline__ double ldtab(const double* p) {
+#if defined(SWE_TABLE_EVICT_FIRST)
+  double v;
+  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.f64 %0, [%1], %2;"
+      : "=d"(v) : "l"(p), "l"(l2_evict_first_policy()));
+  return v;
+#elif defined(SWE_TABLE_NOALLOC)
+  double v;
+  asm("ld.global.nc.L1::no_allocate.f64 %0, [%1];" : "=d"(v) : "l"(p));
+  return v;
+#else
+  return __ldg(p);
+#endif
+}
+__device__ __forceinline__ int ldtabi(const int32_t* p) {
+#if defined(SWE_TABLE_EVICT_FIRST)
+  int v;
+  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.s32 %0, [%1], %2;"
+      : "=r"(v) : "l"(p), "l"(l2_evict_first_policy()));
+  return v;
+#elif defined(SWE_TABLE_NOALLOC)
+  int v;
+  asm("ld.global.nc.L1::no_allocate.s32 %0, [%1];" : "=r"(v) : "l"(p));
+  return v;
+#else
+  return __ldg(p);
+#endif
+}
 
 // L psi at cell i for one plane: wld_i psi_i + sum_k wl_k psi_{nbr_k}
 __device__ __forceinline__ double lap_cell(const Tables& T, int i, const int (&nb)[SLOTS],
                                            const double* psi) {
-  double acc = ldro(T.wld + i) * ld(psi + i);
+  double acc = ldtab(T.wld + i) * ld(psi + i);
 #pragma unroll
-  for (int k = 0; k < SLOTS; ++k) acc = fma(ldro(T.wl + (size_t)k * T.ng + i), ld(psi + nb[k]), acc);
+  for (int k = 0; k < SLOTS; ++k) acc = fma(ldtab(T.wl + (size_t)k * T.ng + i), ld(psi + nb[k]), acc);
   return acc;
 }
 
 __device__ __forceinline__ void load_nbr(const Tables& T, int i, int (&nb)[SLOTS]) {
 #pragma unroll
-  for (int k = 0; k < SLOTS; ++k) nb[k] = __ldg(T.nbr + (size_t)k * T.ng + i);
+  for (int k = 0; k < SLOTS; ++k) nb[k] = ldtabi(T.nbr + (size_t)k * T.ng + i);
 }
 
-// Pass 1 of a stencil at cell i; writes the 8 intermediate planes of tmp.
-//   MODE_F: x = u.          tmp = [L u (4), E = |u|^2/2 + g h, q = u h]
-//   MODE_J: x = sx * xraw.  tmp = [L x (4), s = u.x_u + g x_h, q = x_u h + u x_h]
-//   MODE_Q: x = d.          tmp = [-, -, -, -, E = |d_u|^2/2, q = d_u d_h]
+// Pass 1 of a stencil at cell i.  Writes four Laplacian planes to Lout and
+// the scalar and vector planes to sq (4 planes: scalar, vector x, y, z):
+//   MODE_F: x = u.          L u (4), E = |u|^2/2 + g h, q = u h
+//   MODE_J: x = sx * xraw.  L x (4), s = u.x_u + g x_h,  q = x_u h + u x_h
+//   MODE_Q: x = d.          -,       E = |d_u|^2/2,      q = d_u d_h
 template <int MODE>
 __device__ __forceinline__ void pass1_cell(const Tables& T, int i, const double* x, double sx,
-                                           const double* u, double* tmp) {
+                                           const double* u, double* Lout, double* sq) {
   const int ng = T.ng;
   int nb[SLOTS];
   load_nbr(T, i, nb);
@@ -68,7 +108,7 @@ __device__ __forceinline__ void pass1_cell(const Tables& T, int i, const double*
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       double lx = lap_cell(T, i, nb, x + (size_t)c * ng);
-      tmp[(size_t)c * ng + i] = (MODE == MODE_J) ? sx * lx : lx;
+      Lout[(size_t)c * ng + i] = (MODE == MODE_J) ? sx * lx : lx;
     }
   }
   if (MODE == MODE_J) {
@@ -78,52 +118,95 @@ __device__ __forceinline__ void pass1_cell(const Tables& T, int i, const double*
 #pragma unroll
     for (int c = 0; c < 4; ++c) uv[c] = ldro(u + (size_t)c * ng + i);
     double s = fma(uv[0], xv[0], fma(uv[1], xv[1], fma(uv[2], xv[2], T.g * xv[3])));
-    tmp[(size_t)4 * ng + i] = s;
+    sq[i] = s;
 #pragma unroll
-    for (int c = 0; c < 3; ++c) tmp[(size_t)(5 + c) * ng + i] = fma(xv[c], uv[3], uv[c] * xv[3]);
+    for (int c = 0; c < 3; ++c) sq[(size_t)(1 + c) * ng + i] = fma(xv[c], uv[3], uv[c] * xv[3]);
   } else if (MODE == MODE_F) {
     double e = fma(0.5, fma(xv[0], xv[0], fma(xv[1], xv[1], xv[2] * xv[2])), T.g * xv[3]);
-    tmp[(size_t)4 * ng + i] = e;
+    sq[i] = e;
 #pragma unroll
-    for (int c = 0; c < 3; ++c) tmp[(size_t)(5 + c) * ng + i] = xv[c] * xv[3];
+    for (int c = 0; c < 3; ++c) sq[(size_t)(1 + c) * ng + i] = xv[c] * xv[3];
   } else {
     double e = 0.5 * fma(xv[0], xv[0], fma(xv[1], xv[1], xv[2] * xv[2]));
-    tmp[(size_t)4 * ng + i] = e;
+    sq[i] = e;
 #pragma unroll
-    for (int c = 0; c < 3; ++c) tmp[(size_t)(5 + c) * ng + i] = xv[c] * xv[3];
+    for (int c = 0; c < 3; ++c) sq[(size_t)(1 + c) * ng + i] = xv[c] * xv[3];
   }
+}
+
+// Fused IOM2 orthogonalisation and pass 1 (MODE_J) at cell i.  z is A v_j
+// (complete on every cell), r_j and r_m the raw basis vectors j and j-1 with
+// their Laplacian planes Lj, Lm; aj, am the window coefficients with the
+// basis scales folded in (am = 0 and r_m, Lm unused for j = 0):
+//   z' = z - aj r_j - am r_m                          -> rnew (own cell)
+//   L z' = L z - aj L r_j - am L r_m                  -> Lnew (L is linear)
+//   s', q' of z'                                      -> sq
+// and returns |z'|^2 of the cell.  No value of z' is gathered, so rnew may be
+// written while neighbours still read z.
+__device__ __forceinline__ double orth_pass1_cell(const Tables& T, int i, const double* z,
+                                                  const double* rj, const double* rm, double aj,
+                                                  double am, const double* Lj, const double* Lm,
+                                                  double* rnew, double* Lnew, const double* u,
+                                                  double* sq) {
+  const int ng = T.ng;
+  int nb[SLOTS];
+  load_nbr(T, i, nb);
+  double zp[4], nrm = 0.0;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const size_t e = (size_t)c * ng + i;
+    double v = fma(-aj, ld(rj + e), ld(z + e));
+    double lz = fma(-aj, ld(Lj + e), lap_cell(T, i, nb, z + (size_t)c * ng));
+    if (rm) {
+      v = fma(-am, ld(rm + e), v);
+      lz = fma(-am, ld(Lm + e), lz);
+    }
+    zp[c] = v;
+    rnew[e] = v;
+    Lnew[e] = lz;
+    nrm = fma(v, v, nrm);
+  }
+  double uv[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) uv[c] = ldro(u + (size_t)c * ng + i);
+  sq[i] = fma(uv[0], zp[0], fma(uv[1], zp[1], fma(uv[2], zp[2], T.g * zp[3])));
+#pragma unroll
+  for (int c = 0; c < 3; ++c) sq[(size_t)(1 + c) * ng + i] = fma(zp[c], uv[3], uv[c] * zp[3]);
+  return nrm;
 }
 
 // Pass 2 of a stencil at cell i: out[4] = F(u), J(u)x or Q(d) at cell i.
 //   x: the same vector as pass 1 (F: u, J: raw x with scale sx, Q: d)
+//   Lp, sq: the planes pass 1 wrote (Laplacian, scalar + vector)
 //   aux (MODE_J only): [eta, P_x, P_y, P_z] of the linearisation state,
 //   eta = V u + f, P = n x u.
 template <int MODE>
 __device__ __forceinline__ void pass2_cell(const Tables& T, int i, const double* x, double sx,
-                                           const double* tmp, const double* aux, double out[4]) {
+                                           const double* Lp, const double* sq, const double* aux,
+                                           double out[4]) {
   const int ng = T.ng;
   int nb[SLOTS];
   load_nbr(T, i, nb);
   // relative vorticity of x: V . x_u
   double vor = 0.0;
 #pragma unroll
-  for (int c = 0; c < 3; ++c) vor = fma(ldro(T.vd + (size_t)c * ng + i), ld(x + (size_t)c * ng + i), vor);
+  for (int c = 0; c < 3; ++c) vor = fma(ldtab(T.vd + (size_t)c * ng + i), ld(x + (size_t)c * ng + i), vor);
 #pragma unroll
   for (int k = 0; k < SLOTS; ++k) {
     const int j = nb[k];
 #pragma unroll
     for (int c = 0; c < 3; ++c)
-      vor = fma(ldro(T.vc + ((size_t)c * SLOTS + k) * ng + i), ld(x + (size_t)c * ng + j), vor);
+      vor = fma(ldtab(T.vc + ((size_t)c * SLOTS + k) * ng + i), ld(x + (size_t)c * ng + j), vor);
   }
   // raw gradient of the scalar plane and divergence of the vector planes
-  const double* sc = tmp + (size_t)4 * ng;
+  const double* sc = sq;
   const double sci = ld(sc + i);
   double gr[3], dv = 0.0;
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    double nd = ldro(T.ndd + (size_t)c * ng + i);
-    gr[c] = (nd - ldro(T.sdg + (size_t)c * ng + i)) * sci;
-    dv = fma(nd, ld(tmp + (size_t)(5 + c) * ng + i), dv);
+    double nd = ldtab(T.ndd + (size_t)c * ng + i);
+    gr[c] = ldtab(T.gdg + (size_t)c * ng + i) * sci;
+    dv = fma(nd, ld(sq + (size_t)(1 + c) * ng + i), dv);
   }
 #pragma unroll
   for (int k = 0; k < SLOTS; ++k) {
@@ -131,12 +214,12 @@ __device__ __forceinline__ void pass2_cell(const Tables& T, int i, const double*
     const double scj = ld(sc + j);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      double w = ldro(T.nc + ((size_t)c * SLOTS + k) * ng + i);
+      double w = ldtab(T.nc + ((size_t)c * SLOTS + k) * ng + i);
       gr[c] = fma(w, scj, gr[c]);
-      dv = fma(w, ld(tmp + (size_t)(5 + c) * ng + j), dv);
+      dv = fma(w, ld(sq + (size_t)(1 + c) * ng + j), dv);
     }
   }
-  double n0 = ldro(T.nrm + i), n1 = ldro(T.nrm + ng + i), n2 = ldro(T.nrm + 2 * (size_t)ng + i);
+  double n0 = ldtab(T.nrm + i), n1 = ldtab(T.nrm + ng + i), n2 = ldtab(T.nrm + 2 * (size_t)ng + i);
   double ng_ = fma(n0, gr[0], fma(n1, gr[1], n2 * gr[2]));
   gr[0] = fma(-n0, ng_, gr[0]);
   gr[1] = fma(-n1, ng_, gr[1]);
@@ -173,7 +256,7 @@ __device__ __forceinline__ void pass2_cell(const Tables& T, int i, const double*
   }
   if (MODE != MODE_Q) {  // dissipation -nu L (L x) on every variable
 #pragma unroll
-    for (int c = 0; c < 4; ++c) out[c] = fma(-T.nu, lap_cell(T, i, nb, tmp + (size_t)c * ng), out[c]);
+    for (int c = 0; c < 4; ++c) out[c] = fma(-T.nu, lap_cell(T, i, nb, Lp + (size_t)c * ng), out[c]);
   }
 }
 

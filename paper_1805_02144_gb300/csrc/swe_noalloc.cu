@@ -52,14 +52,14 @@ __global__ void k_aux_na(Tables T, const double* __restrict__ u, double* aux) {
 
 __global__ void k_pass1_na(Tables T, const double* x, const double* u, double* tmp) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < T.ng; i += gridDim.x * blockDim.x)
-    pass1_cell<MODE_J>(T, i, x, 1.0, u, tmp);
+    pass1_cell<MODE_J>(T, i, x, 1.0, u, tmp, tmp + (size_t)4 * T.ng);
 }
 
 __global__ void k_pass2_na(Tables T, const double* x, const double* tmp, const double* aux, double* out) {
   const int ng = T.ng;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ng; i += gridDim.x * blockDim.x) {
     double o[4];
-    pass2_cell<MODE_J>(T, i, x, 1.0, tmp, aux, o);
+    pass2_cell<MODE_J>(T, i, x, 1.0, tmp, tmp + (size_t)4 * ng, aux, o);
 #pragma unroll
     for (int c = 0; c < 4; ++c) out[(size_t)c * ng + i] = o[c];
   }
