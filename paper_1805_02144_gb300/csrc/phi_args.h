@@ -46,6 +46,13 @@ struct PhiCtrl {
   int n_iter, n_wjv, comb_terms, pad;
 };
 
+// The persistent-kernel instantiation chosen for a grid.
+struct PhiLaunch {
+  const void* fn = nullptr;
+  int threads = 0;
+  int nblocks = 0;
+};
+
 struct PhiArgs {
   Tables T;
   const double* u_lin;      // [4][ng] linearisation state (read-only)

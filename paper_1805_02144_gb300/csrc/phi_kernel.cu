@@ -25,13 +25,7 @@
 
 namespace swe {
 
-#ifndef PHI_MIN_BLOCKS
-#define PHI_MIN_BLOCKS 2
-#endif
-#ifndef PHI_BLOCK_THREADS
-#define PHI_BLOCK_THREADS 256
-#endif
-constexpr int PHI_THREADS = PHI_BLOCK_THREADS;
+constexpr int PHI_MAX_THREADS = 256;  // largest block size of any instantiation
 constexpr double TAYLOR_THETA = 4.0;
 
 __device__ __forceinline__ double vld(const double* p) { return *(volatile const double*)p; }
@@ -41,24 +35,13 @@ struct Range {
   int c0, c1;
 };
 
-// Cells of this thread inside the block's range.  Default: block-strided.
-// SWE_WARP_CHUNKS: each warp owns a contiguous, equal share of the range (the
-// remainder spread over the warps), lanes strided inside it.
+// Cells of this thread inside the block's range (block-strided).
 struct CellLoop {
   int first, end, step;
   __device__ CellLoop(const Range& R) {
-#ifdef SWE_WARP_CHUNKS
-    const int W = PHI_THREADS / 32, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const long long C = R.c1 - R.c0;
-    const int ws = R.c0 + (int)(C * w / W), we = R.c0 + (int)(C * (w + 1) / W);
-    first = ws + lane;
-    end = we;
-    step = 32;
-#else
     first = R.c0 + threadIdx.x;
     end = R.c1;
-    step = PHI_THREADS;
-#endif
+    step = blockDim.x;
   }
 };
 #define FOR_CELLS(i) for (int i = CL.first; i < CL.end; i += CL.step)
@@ -80,7 +63,7 @@ __device__ __forceinline__ void block_sum(double (&v)[K], double* sred) {
   if (threadIdx.x == 0) {
     for (int k = 0; k < K; ++k) {
       double s = 0.0;
-      for (int w = 0; w < PHI_THREADS / 32; ++w) s += sred[w * NRED + k];
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sred[w * NRED + k];
       v[k] = s;
     }
   }
@@ -94,7 +77,7 @@ enum Phase { PH_PROLOGUE = 0, PH_W_PASS1, PH_W_PASS2, PH_K_PASS1, PH_K_PASS2, PH
 
 struct Shared {
   unsigned long long t_last;
-  double red[(PHI_THREADS / 32) * NRED];
+  double red[(PHI_MAX_THREADS / 32) * NRED];
   double coef[KMAX + PMAX + 4];
   int last;
   int ok;
@@ -151,7 +134,7 @@ __device__ bool grid_reduce(const PhiArgs& a, Shared& sh, double (&v)[K], int ph
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       double s = 0.0;
-      for (int b = threadIdx.x; b < (int)gridDim.x; b += PHI_THREADS) s += a.part[(size_t)b * NRED + k];
+      for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) s += a.part[(size_t)b * NRED + k];
       tot[k] = s;
     }
     block_sum<K>(tot, sh.red);
@@ -298,7 +281,7 @@ __device__ void decide(const PhiArgs& a, Shared& sh) {
   double eps = 0.0, hnorm = 1.0, hnext = 0.0;
   if (beta > 0.0) {
     m_use = min(m, (int)C->size);
-    for (int r = lane; r <= m_use; r += PHI_THREADS) {
+    for (int r = lane; r <= m_use; r += blockDim.x) {
       sh.hd[r] = C->hd[r];
       sh.hu[r] = C->hu[r];
       sh.hl[r] = C->hl[r];
@@ -329,7 +312,7 @@ __device__ void decide(const PhiArgs& a, Shared& sh) {
   if (accepted) {
     const double tp = pow(tau_k, (double)p);
     if (beta > 0.0) {
-      for (int r = lane; r < m_use; r += PHI_THREADS) C->cV[r] = tp * beta * sh.y[r] * C->sig[r];
+      for (int r = lane; r < m_use; r += blockDim.x) C->cV[r] = tp * beta * sh.y[r] * C->sig[r];
       if (lane == 0)
         C->cV[m_use] = hnext != 0.0 ? tp * beta * tau_k * hnext * sh.x[m_use - 1] * C->sig[m_use] : 0.0;
     }
@@ -434,7 +417,7 @@ __device__ void decide(const PhiArgs& a, Shared& sh) {
 // ---------------------------------------------------------------------------
 // the kernel
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(PHI_THREADS, PHI_MIN_BLOCKS) phi_kernel(const __grid_constant__ PhiArgs a) {
+__device__ __forceinline__ void phi_body(const PhiArgs& a) {
   __shared__ Shared sh;
   const Tables& T = a.T;
   const int ng = T.ng;
@@ -648,8 +631,8 @@ __global__ void __launch_bounds__(PHI_THREADS, PHI_MIN_BLOCKS) phi_kernel(const 
 
         // ---- y_{k+1} = tau^p phi_p(tau A) w_p + sum_{j<p} tau^j/j! w_j (eq3.17)
         const int ncomb = vldi(&C->ncomb);
-        for (int r = threadIdx.x; r < ncomb; r += PHI_THREADS) sh.coef[r] = vld(&C->cV[r]);
-        for (int r = threadIdx.x; r < p; r += PHI_THREADS) sh.coef[KMAX + 2 + r] = vld(&C->cW[r]);
+        for (int r = threadIdx.x; r < ncomb; r += blockDim.x) sh.coef[r] = vld(&C->cV[r]);
+        for (int r = threadIdx.x; r < p; r += blockDim.x) sh.coef[KMAX + 2 + r] = vld(&C->cW[r]);
         __syncthreads();
         const bool land = vldi(&C->land) != 0;
         double* yo = land ? a.y_out[oi] : nullptr;
@@ -695,45 +678,73 @@ finish:
   }
 }
 
-// Cooperative launch (all blocks co-resident: the grid barriers need it).
-// With a non-empty table window the operator tables get a persisting L2
-// access policy for this launch, so they stay cached next to the vectors.
-int launch_phi_kernel(const PhiArgs& a, int nblocks, cudaStream_t stream, const void* tab_base,
-                      size_t tab_bytes) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(nblocks);
-  cfg.blockDim = dim3(PHI_THREADS);
-  cfg.dynamicSmemBytes = 0;
-  cfg.stream = stream;
-  cudaLaunchAttribute attr[2];
-  int na = 0;
-  attr[na].id = cudaLaunchAttributeCooperative;
-  attr[na].val.cooperative = 1;
-  ++na;
-  if (tab_base && tab_bytes > 0) {
-    attr[na].id = cudaLaunchAttributeAccessPolicyWindow;
-    attr[na].val.accessPolicyWindow.base_ptr = const_cast<void*>(tab_base);
-    attr[na].val.accessPolicyWindow.num_bytes = tab_bytes;
-    attr[na].val.accessPolicyWindow.hitRatio = 1.0f;
-    attr[na].val.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
-    attr[na].val.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
-    ++na;
-  }
-  cfg.attrs = attr;
-  cfg.numAttrs = na;
-  cudaError_t e = cudaLaunchKernelEx(&cfg, phi_kernel, a);
-  return e == cudaSuccess ? 0 : (int)e;
+// Instantiations (block size, minimum resident blocks per SM for the register
+// budget).  The body adapts to blockDim.x; the taylor exponential needs at
+// least m_max + p + 1 = 69 threads.
+template <int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) phi_kernel(const __grid_constant__ PhiArgs a) {
+  phi_body(a);
 }
 
-int phi_kernel_max_blocks(int* nblocks) {
-  int dev = 0, nsm = 0, per = 0;
+struct PhiVariant {
+  const void* fn;
+  int threads;
+};
+static const PhiVariant kVariants[] = {
+    {(const void*)phi_kernel<256, 2>, 256},
+    {(const void*)phi_kernel<192, 2>, 192},
+    {(const void*)phi_kernel<128, 3>, 128},
+    {(const void*)phi_kernel<96, 4>, 96},
+};
+
+// Picks the instantiation and block count for a grid of ng cells.  The FP64
+// unit charges a whole warp slot per warp instruction however many lanes are
+// active, so the cost of a stencil phase on the busiest SM is proportional to
+// (resident blocks) x (rounds of blockDim cells per block) x (warps per
+// block); the variant with the fewest such warp-rounds wins (ties: larger
+// blocks, fewer barriers participants).  Small grids use fewer blocks.
+int phi_select(int ng, PhiLaunch* out) {
+  int dev = 0, nsm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return -1;
   if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -1;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, phi_kernel, PHI_THREADS, 0) != cudaSuccess)
-    return -1;
-  if (per < 1) return -1;
-  *nblocks = nsm * per;
-  return 0;
+  long long best = -1;
+  for (const PhiVariant& v : kVariants) {
+    int per = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, v.fn, v.threads, 0) != cudaSuccess || per < 1)
+      continue;
+    long long nb = (long long)per * nsm;
+    long long need = (ng + v.threads - 1) / v.threads;
+    if (need < nb) nb = need;
+    if (nb < 1) nb = 1;
+    long long cells = (ng + nb - 1) / nb;
+    long long rounds = (cells + v.threads - 1) / v.threads;
+    long long per_sm = (nb + nsm - 1) / nsm;
+    long long cost = per_sm * rounds * (v.threads / 32);
+    if (best < 0 || cost < best) {
+      best = cost;
+      out->fn = v.fn;
+      out->threads = v.threads;
+      out->nblocks = (int)nb;
+    }
+  }
+  return best < 0 ? -1 : 0;
+}
+
+// Cooperative launch (all blocks co-resident: the grid barriers need it).
+int launch_phi_kernel(const PhiLaunch& L, const PhiArgs& a, cudaStream_t stream) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(L.nblocks);
+  cfg.blockDim = dim3(L.threads);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  void* args[] = {(void*)&a};
+  cudaError_t e = cudaLaunchKernelExC(&cfg, L.fn, args);
+  return e == cudaSuccess ? 0 : (int)e;
 }
 
 }  // namespace swe

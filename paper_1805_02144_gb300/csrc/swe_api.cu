@@ -15,9 +15,8 @@
 #include "swe_dev.cuh"
 
 namespace swe {
-int launch_phi_kernel(const PhiArgs& a, int nblocks, cudaStream_t stream, const void* tab_base,
-                      size_t tab_bytes);
-int phi_kernel_max_blocks(int* nblocks);
+int launch_phi_kernel(const PhiLaunch& L, const PhiArgs& a, cudaStream_t stream);
+int phi_select(int ng, PhiLaunch* out);
 }  // namespace swe
 
 using namespace swe;
@@ -70,9 +69,8 @@ struct swe_grid {
   DevAttempt* trace = nullptr;
   double* replay = nullptr;
   int replay_cap = 0;
-  int nblocks = 0;
+  PhiLaunch launch;          // persistent-kernel instantiation for this grid
   size_t tab_bytes = 0;      // size of the table allocation
-  size_t l2_window = 0;      // persisting-L2 window over the tables (0: none)
   // profiling (swe_profile_enable)
   bool prof_on = false;
   DevProfile* dprof = nullptr;
@@ -266,9 +264,8 @@ int upload_grid(swe_grid* g) {
 int ensure_workspace(swe_grid* g) {
   if (!g->dtab) return fail(SWE_ERR_INVALID_ARG, "grid was built on the host only");
   if (g->dws) return SWE_OK;
-  int nb = 0;
-  if (phi_kernel_max_blocks(&nb) != 0) return fail(SWE_ERR_CUDA, "occupancy query for phi kernel failed");
-  g->nblocks = nb;
+  if (phi_select(g->T.ng, &g->launch) != 0) return fail(SWE_ERR_CUDA, "occupancy query for phi kernel failed");
+  const int nb = g->launch.nblocks;
   const size_t ng = g->T.ng, n = 4 * ng;
   size_t sizes[] = {
       (size_t)(KMAX + 1) * n * 8,  // Vbuf
@@ -301,22 +298,6 @@ int ensure_workspace(swe_grid* g) {
   }
   g->ws_bytes = total;
   CK(cudaMemset(g->dws, 0, total));
-#ifdef SWE_L2_PERSIST
-  {
-    // Reserve persisting L2 for the operator tables (a limit of this
-    // process's context, released with it) and window the persistent launch.
-    int dev = 0, max_persist = 0, max_window = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, dev);
-    cudaDeviceGetAttribute(&max_window, cudaDevAttrMaxAccessPolicyWindowSize, dev);
-    size_t want = g->tab_bytes;
-    if (want > (size_t)max_persist) want = (size_t)max_persist;
-    if (want > (size_t)max_window) want = (size_t)max_window;
-    if (want > 0 && cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want) == cudaSuccess)
-      g->l2_window = want;
-    cudaGetLastError();
-  }
-#endif
   return SWE_OK;
 }
 
@@ -387,7 +368,7 @@ int phi_call(swe_grid* g, const double* u_lin, double dt, int p, const double* c
   a.prof = g->prof_on ? g->dprof : nullptr;
   CK(cudaMemsetAsync(g->sync, 0, sizeof(GridSync), st));
   ProfSpan span(g, st, &g->phi_ev);
-  int e = launch_phi_kernel(a, g->nblocks, st, g->l2_window ? g->dtab : nullptr, g->l2_window);
+  int e = launch_phi_kernel(g->launch, a, st);
   if (e != 0) return cuda_fail((cudaError_t)e, "cudaLaunchCooperativeKernel(phi_kernel)");
   span.finish();
   count_launches(g, 1);

@@ -36,44 +36,25 @@ enum StencilMode { MODE_F = 0, MODE_J = 1, MODE_Q = 2 };
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double ld(const double* p) { return *p; }
 __device__ __forceinline__ double ldro(const double* p) { return __ldg(p); }
-// Operator tables are read once per cell and pass: with SWE_TABLE_NOALLOC they
-// bypass L1 allocation so that L1 keeps the gathered vectors.
-// With SWE_TABLE_EVICT_FIRST they are also marked first to leave L2, so the
-// gathered vectors (written one phase earlier) stay L2-resident.
-#if defined(SWE_TABLE_EVICT_FIRST)
+// Operator tables are read once per cell and pass: they bypass L1 allocation
+// and are marked first to leave L2, so that L1 and L2 keep the gathered
+// vectors (written one phase earlier).
 __device__ __forceinline__ unsigned long long l2_evict_first_policy() {
   unsigned long long pol;
   asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
   return pol;
 }
-#endif
 __device__ __forceinline__ double ldtab(const double* p) {
-#if defined(SWE_TABLE_EVICT_FIRST)
   double v;
   asm("ld.global.nc.L1::no_allocate.L2::cache_hint.f64 %0, [%1], %2;"
       : "=d"(v) : "l"(p), "l"(l2_evict_first_policy()));
   return v;
-#elif defined(SWE_TABLE_NOALLOC)
-  double v;
-  asm("ld.global.nc.L1::no_allocate.f64 %0, [%1];" : "=d"(v) : "l"(p));
-  return v;
-#else
-  return __ldg(p);
-#endif
 }
 __device__ __forceinline__ int ldtabi(const int32_t* p) {
-#if defined(SWE_TABLE_EVICT_FIRST)
   int v;
   asm("ld.global.nc.L1::no_allocate.L2::cache_hint.s32 %0, [%1], %2;"
       : "=r"(v) : "l"(p), "l"(l2_evict_first_policy()));
   return v;
-#elif defined(SWE_TABLE_NOALLOC)
-  int v;
-  asm("ld.global.nc.L1::no_allocate.s32 %0, [%1];" : "=r"(v) : "l"(p));
-  return v;
-#else
-  return __ldg(p);
-#endif
 }
 
 // L psi at cell i for one plane: wld_i psi_i + sum_k wl_k psi_{nbr_k}
