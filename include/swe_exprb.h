@@ -65,6 +65,12 @@ typedef struct {
                             when non-NULL the step sizes, Krylov sizes and decisions
                             are taken from it instead of the controller            */
   int n_replay;      /* number of attempts in replay                               */
+  int precision;     /* 0: FP64 throughout.  1: mixed -- stencils, Krylov basis and
+                        stage vectors of the phi evaluations in FP32 (FP32 operator
+                        tables); reductions (partial sums per thread in FP32 over at
+                        most a few dozen terms, then FP64), norms, controller and
+                        exponential in FP64; F(u_n), D_ni and the state update in
+                        FP64.  Public vectors stay FP64 either way.                 */
 } phi_opts;
 
 /* One controller attempt (trace record). */

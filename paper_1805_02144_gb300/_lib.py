@@ -32,7 +32,8 @@ class PhiOptsC(C.Structure):
     _fields_ = [("tol", C.c_double), ("tol_mode", C.c_int), ("m_init", C.c_int),
                 ("m_max", C.c_int), ("iom", C.c_int), ("delta", C.c_double),
                 ("gamma", C.c_double), ("kappa", C.c_double), ("max_reject", C.c_int),
-                ("m_carry", C.c_int), ("replay", C.POINTER(C.c_double)), ("n_replay", C.c_int)]
+                ("m_carry", C.c_int), ("replay", C.POINTER(C.c_double)), ("n_replay", C.c_int),
+                ("precision", C.c_int)]
 
 
 class PhiAttemptC(C.Structure):

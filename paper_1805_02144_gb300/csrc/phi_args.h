@@ -53,21 +53,25 @@ struct PhiLaunch {
   int nblocks = 0;
 };
 
-struct PhiArgs {
-  Tables T;
-  const double* u_lin;      // [4][ng] linearisation state (read-only)
-  const double* aux;        // [4][ng] eta and n x u of u_lin
+// Arguments of one persistent launch.  R is the precision of tables, vectors
+// and stencil arithmetic (double: FP64 path; float: mixed path, whose
+// reductions, control block, exponential and controller stay in double).
+template <typename R>
+struct PhiArgsT {
+  TablesT<R> T;
+  const R* u_lin;           // [4][ng] linearisation state (read-only)
+  const R* aux;             // [4][ng] eta and n x u of u_lin
   double dt;
   int p, ns;
   double rho[NSMAX];
-  const double* v[PMAX + 1];   // device, nullptr = zero
-  double* y_out[NSMAX];
+  const R* v[PMAX + 1];     // device, nullptr = zero
+  R* y_out[NSMAX];
   // workspace
-  double* Vbuf;             // (KMAX + 1) raw basis slots of n doubles (slot 0 unused)
-  double* W;                // (PMAX + 1) x n: W[0] = y_k, W[j] = w_j
-  double* tmp;              // 8 x ng pass-1 planes (Laplacian 4, scalar/vector 4)
-  double* Lring;            // 3 x n: Laplacian planes of the last three raw slots
-  double* Zbuf;             // n: A v_j before orthogonalisation
+  R* Vbuf;                  // (KMAX + 1) raw basis slots of n values (slot 0 unused)
+  R* W;                     // (PMAX + 1) x n: W[0] = y_k, W[j] = w_j
+  R* tmp;                   // 8 x ng pass-1 planes (Laplacian 4, scalar/vector 4)
+  R* Lring;                 // 3 x n: Laplacian planes of the last three raw slots
+  R* Zbuf;                  // n: A v_j before orthogonalisation
   double* part;             // nblocks x NRED partial sums
   PhiCtrl* ctrl;
   GridSync* sync;
@@ -84,5 +88,7 @@ struct PhiArgs {
   int tol_mode, m_init, m_max, max_reject;
   int64_t nA;
 };
+using PhiArgs = PhiArgsT<double>;
+using PhiArgsF = PhiArgsT<float>;
 
 }  // namespace swe

@@ -79,6 +79,7 @@ struct Shared {
   unsigned long long t_last;
   double red[(PHI_MAX_THREADS / 32) * NRED];
   double coef[KMAX + PMAX + 4];
+  float coeff[KMAX + PMAX + 4];
   int last;
   int ok;
   unsigned int gen;
@@ -89,7 +90,8 @@ struct Shared {
   double scal[4];
 };
 
-__device__ __forceinline__ void phase_tick(const PhiArgs& a, Shared& sh, int phase) {
+template <class A>
+__device__ __forceinline__ void phase_tick(const A& a, Shared& sh, int phase) {
   if (a.prof && blockIdx.x == 0 && threadIdx.x == 0) {
     unsigned long long now = globaltimer();
     a.prof->phase_ns[phase] += (long long)(now - sh.t_last);
@@ -99,7 +101,8 @@ __device__ __forceinline__ void phase_tick(const PhiArgs& a, Shared& sh, int pha
 
 // Plain grid barrier.  Returns false (uniformly per block) when the launch is
 // being aborted.
-__device__ bool grid_barrier(const PhiArgs& a, Shared& sh, int phase) {
+template <class A>
+__device__ bool grid_barrier(const A& a, Shared& sh, int phase) {
   __syncthreads();
   if (threadIdx.x == 0) {
     bool last;
@@ -119,8 +122,8 @@ __device__ bool grid_barrier(const PhiArgs& a, Shared& sh, int phase) {
 // Grid reduction of K per-thread partials, then a barrier.  The last block
 // to arrive sums the block partials in block order, stores them in
 // ctrl->red[], runs post(ctrl) on its thread 0, and releases the barrier.
-template <int K, class Post>
-__device__ bool grid_reduce(const PhiArgs& a, Shared& sh, double (&v)[K], int phase, Post post) {
+template <int K, class A, class Post>
+__device__ bool grid_reduce(const A& a, Shared& sh, double (&v)[K], int phase, Post post) {
   block_sum<K>(v, sh.red);
   if (threadIdx.x == 0) {
     for (int k = 0; k < K; ++k) a.part[(size_t)blockIdx.x * NRED + k] = v[k];
@@ -154,11 +157,13 @@ __device__ bool grid_reduce(const PhiArgs& a, Shared& sh, double (&v)[K], int ph
   return sh.ok;
 }
 
-__device__ __forceinline__ void abort_launch(const PhiArgs& a, int code) {
+template <class A>
+__device__ __forceinline__ void abort_launch(const A& a, int code) {
   atomicCAS(&a.sync->abort, 0, code);
 }
 
-__device__ __forceinline__ double* raw_slot(const PhiArgs& a, int j) {
+template <typename R>
+__device__ __forceinline__ R* raw_slot(const PhiArgsT<R>& a, int j) {
   const size_t n = (size_t)4 * a.T.ng;
   return j == 0 ? a.W + (size_t)a.p * n : a.Vbuf + (size_t)j * n;
 }
@@ -247,7 +252,8 @@ __device__ double cost_fn(double tau, int m, int p, double remaining, double N, 
 // Error estimate, acceptance test and controller (Algorithm 1 steps 2(ii)-6),
 // executed by all threads of block 0 (uniform control flow; the scalar
 // controller runs on thread 0).  Writes the decision into ctrl.
-__device__ void decide(const PhiArgs& a, Shared& sh) {
+template <class A>
+__device__ void decide(const A& a, Shared& sh) {
   volatile PhiCtrl* C = a.ctrl;
   const int lane = threadIdx.x;
   const int p = a.p;
@@ -417,15 +423,26 @@ __device__ void decide(const PhiArgs& a, Shared& sh) {
 // ---------------------------------------------------------------------------
 // the kernel
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void phi_body(const PhiArgs& a) {
+template <typename R>
+__device__ __forceinline__ R shared_coef(const Shared& sh, int r);
+template <>
+__device__ __forceinline__ double shared_coef<double>(const Shared& sh, int r) { return sh.coef[r]; }
+template <>
+__device__ __forceinline__ float shared_coef<float>(const Shared& sh, int r) { return sh.coeff[r]; }
+
+template <typename R>
+__device__ __forceinline__ void phi_body(const PhiArgsT<R>& a) {
   __shared__ Shared sh;
-  const Tables& T = a.T;
+  const TablesT<R>& T = a.T;
+  // happy-breakdown threshold relative to the window coefficients: near the
+  // rounding floor of the basis precision
+  const double bd = sizeof(R) == 8 ? 1e-13 : 1e-6;
   const int ng = T.ng;
   const size_t n = (size_t)4 * ng;
   const int p = a.p;
   const int chunk = (ng + gridDim.x - 1) / gridDim.x;
-  const Range R{min(ng, (int)blockIdx.x * chunk), min(ng, ((int)blockIdx.x + 1) * chunk)};
-  const CellLoop CL(R);
+  const Range RG{min(ng, (int)blockIdx.x * chunk), min(ng, ((int)blockIdx.x + 1) * chunk)};
+  const CellLoop CL(RG);
   PhiCtrl* C = a.ctrl;
 
   // ---- prologue: y = v_0, norms of the inputs -----------------------------
@@ -446,12 +463,12 @@ __device__ __forceinline__ void phi_body(const PhiArgs& a) {
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
         const size_t e = (size_t)c * ng + i;
-        double y0 = a.v[0] ? __ldg(a.v[0] + e) : 0.0;
-        a.W[e] = y0;
-        v[0] += (y0 != 0.0) ? 1.0 : 0.0;
+        R yv0 = a.v[0] ? __ldg(a.v[0] + e) : R(0);
+        a.W[e] = yv0;
+        v[0] += (yv0 != R(0)) ? 1.0 : 0.0;
         for (int l = 0; l <= p; ++l)
           if (a.v[l]) {
-            double x = __ldg(a.v[l] + e);
+            double x = (double)__ldg(a.v[l] + e);
             v[1 + l] = fma(x, x, v[1 + l]);
           }
       }
@@ -476,7 +493,7 @@ __device__ __forceinline__ void phi_body(const PhiArgs& a) {
   if (vldi(&C->done)) {
     for (int o = 0; o < a.ns; ++o)
       FOR_CELLS(i)
-        for (int c = 0; c < 4; ++c) a.y_out[o][(size_t)c * ng + i] = 0.0;
+        for (int c = 0; c < 4; ++c) a.y_out[o][(size_t)c * ng + i] = R(0);
     goto finish;
   }
 
@@ -499,28 +516,33 @@ __device__ __forceinline__ void phi_body(const PhiArgs& a) {
           }
         }
         const bool nz_prev = vldi(&C->wnz[j - 1]) != 0;
-        double* wprev = a.W + (size_t)(j - 1) * n;
-        double* wj = a.W + (size_t)j * n;
+        R* wprev = a.W + (size_t)(j - 1) * n;
+        R* wj = a.W + (size_t)j * n;
         if (nz_prev) {
           FOR_CELLS(i)
-            pass1_cell<MODE_J>(T, i, wprev, 1.0, a.u_lin, a.tmp, a.tmp + (size_t)4 * ng);
+            pass1_cell<MODE_J>(T, i, wprev, R(1), a.u_lin, a.tmp, a.tmp + (size_t)4 * ng);
           if (!grid_barrier(a, sh, PH_W_PASS1)) goto finish;
         }
-        double v[2] = {0.0, 0.0};
+        R clr[PMAX + 1];
+        for (int l = 0; l <= p - j; ++l) clr[l] = (R)cl[l];
+        const R dtr = (R)a.dt;
+        int nzc = 0;
+        R sqs = R(0);
         FOR_CELLS(i) {
-          double o[4] = {0.0, 0.0, 0.0, 0.0};
-          if (nz_prev) pass2_cell<MODE_J>(T, i, wprev, 1.0, a.tmp, a.tmp + (size_t)4 * ng, a.aux, o);
+          R o[4] = {R(0), R(0), R(0), R(0)};
+          if (nz_prev) pass2_cell<MODE_J>(T, i, wprev, R(1), a.tmp, a.tmp + (size_t)4 * ng, a.aux, o);
 #pragma unroll
           for (int c = 0; c < 4; ++c) {
             const size_t e = (size_t)c * ng + i;
-            double w = a.dt * o[c];
+            R w = dtr * o[c];
             for (int l = 0; l <= p - j; ++l)
-              if (a.v[j + l]) w = fma(cl[l], __ldg(a.v[j + l] + e), w);
+              if (a.v[j + l]) w = fma(clr[l], __ldg(a.v[j + l] + e), w);
             wj[e] = w;
-            v[0] += (w != 0.0) ? 1.0 : 0.0;
-            v[1] = fma(w, w, v[1]);
+            nzc += (w != R(0)) ? 1 : 0;
+            sqs = fma(w, w, sqs);
           }
         }
+        double v[2] = {(double)nzc, (double)sqs};
         GridSync* gs = a.sync;
         auto post = [gs, j, nz_prev, p](volatile PhiCtrl* c) {
           c->wnz[j] = c->red[0] > 0.0;
@@ -560,48 +582,50 @@ __device__ __forceinline__ void phi_body(const PhiArgs& a) {
           // fused orthogonalisation + pass 1 of the next vector, each ended
           // by one grid reduction.  Pass-1 planes of raw slot j: Laplacian in
           // Lring[j % 3], scalar/vector planes in SQ.
-          double* SQ = a.tmp + (size_t)4 * ng;
+          R* SQ = a.tmp + (size_t)4 * ng;
           while (vldi(&C->size) < m_req && !vldi(&C->broken)) {
             const int j = vldi(&C->size);
-            double* rj = raw_slot(a, j);
-            double* rj1 = raw_slot(a, j + 1);
-            double* rjm = j > 0 ? raw_slot(a, j - 1) : nullptr;
-            double* Lj = a.Lring + (size_t)(j % 3) * n;
-            double* Ljm = a.Lring + (size_t)((j + 2) % 3) * n;
-            double* Lj1 = a.Lring + (size_t)((j + 1) % 3) * n;
+            R* rj = raw_slot(a, j);
+            R* rj1 = raw_slot(a, j + 1);
+            R* rjm = j > 0 ? raw_slot(a, j - 1) : nullptr;
+            R* Lj = a.Lring + (size_t)(j % 3) * n;
+            R* Ljm = a.Lring + (size_t)((j + 2) % 3) * n;
+            R* Lj1 = a.Lring + (size_t)((j + 1) % 3) * n;
             const double sj = vld(&C->sig[j]);
             if (j == 0) {
               FOR_CELLS(i)
-                pass1_cell<MODE_J>(T, i, rj, 1.0, a.u_lin, Lj, SQ);
+                pass1_cell<MODE_J>(T, i, rj, R(1), a.u_lin, Lj, SQ);
               if (!grid_barrier(a, sh, PH_K_PASS1)) goto finish;
             }
-            const double zs = a.dt * sj;
-            double v[2] = {0.0, 0.0};
+            const R zs = (R)(a.dt * sj);
+            R d0 = R(0), d1 = R(0);
             FOR_CELLS(i) {
-              double o[4];
-              pass2_cell<MODE_J>(T, i, rj, 1.0, Lj, SQ, a.aux, o);
+              R o[4];
+              pass2_cell<MODE_J>(T, i, rj, R(1), Lj, SQ, a.aux, o);
 #pragma unroll
               for (int c = 0; c < 4; ++c) {
                 const size_t e = (size_t)c * ng + i;
-                double z = zs * o[c];
+                R z = zs * o[c];
                 a.Zbuf[e] = z;
-                if (rjm) v[0] = fma(z, rjm[e], v[0]);
-                v[1] = fma(z, rj[e], v[1]);
+                if (rjm) d0 = fma(z, rjm[e], d0);
+                d1 = fma(z, rj[e], d1);
               }
             }
+            double v[2] = {(double)d0, (double)d1};
             auto post_dots = [j](volatile PhiCtrl* c) {
               if (j > 0) c->hu[j - 1] = c->sig[j - 1] * c->red[0];
               c->hd[j] = c->sig[j] * c->red[1];
             };
             if (!grid_reduce<2>(a, sh, v, PH_K_PASS2, post_dots)) goto finish;
             // z' = z - h_{j-1,j} v_{j-1} - h_{j,j} v_j with its pass-1 planes
-            const double am = j > 0 ? vld(&C->hu[j - 1]) * vld(&C->sig[j - 1]) : 0.0;
-            const double aj = vld(&C->hd[j]) * sj;
-            double w[1] = {0.0};
+            const R am = j > 0 ? (R)(vld(&C->hu[j - 1]) * vld(&C->sig[j - 1])) : R(0);
+            const R aj = (R)(vld(&C->hd[j]) * sj);
+            R nrm = R(0);
             FOR_CELLS(i)
-              w[0] += orth_pass1_cell(T, i, a.Zbuf, rj, rjm, aj, am, Lj, Ljm, rj1, Lj1, a.u_lin, SQ);
+              nrm += orth_pass1_cell(T, i, a.Zbuf, rj, rjm, aj, am, Lj, Ljm, rj1, Lj1, a.u_lin, SQ);
+            double w[1] = {(double)nrm};
             GridSync* gs = a.sync;
-            auto post_norm = [gs, j](volatile PhiCtrl* c) {
+            auto post_norm = [gs, j, bd](volatile PhiCtrl* c) {
               double hn = sqrt((double)c->red[0]);
               double ref = fabs((double)c->hd[j]) + (j > 0 ? fabs((double)c->hu[j - 1]) : 0.0);
               c->size = j + 1;
@@ -612,7 +636,7 @@ __device__ __forceinline__ void phi_body(const PhiArgs& a) {
                 atomicCAS(&gs->abort, 0, SWE_ERR_NONFINITE);
                 return;
               }
-              if (hn <= 1e-13 * ref) {  // happy breakdown: invariant subspace
+              if (hn <= bd * ref) {  // happy breakdown: invariant subspace
                 c->broken = 1;
                 c->hl[j + 1] = 0.0;
                 c->sig[j + 1] = 0.0;
@@ -631,24 +655,31 @@ __device__ __forceinline__ void phi_body(const PhiArgs& a) {
 
         // ---- y_{k+1} = tau^p phi_p(tau A) w_p + sum_{j<p} tau^j/j! w_j (eq3.17)
         const int ncomb = vldi(&C->ncomb);
-        for (int r = threadIdx.x; r < ncomb; r += blockDim.x) sh.coef[r] = vld(&C->cV[r]);
-        for (int r = threadIdx.x; r < p; r += blockDim.x) sh.coef[KMAX + 2 + r] = vld(&C->cW[r]);
+        for (int r = threadIdx.x; r < ncomb; r += blockDim.x) {
+          sh.coef[r] = vld(&C->cV[r]);
+          sh.coeff[r] = (float)sh.coef[r];
+        }
+        for (int r = threadIdx.x; r < p; r += blockDim.x) {
+          sh.coef[KMAX + 2 + r] = vld(&C->cW[r]);
+          sh.coeff[KMAX + 2 + r] = (float)sh.coef[KMAX + 2 + r];
+        }
         __syncthreads();
         const bool land = vldi(&C->land) != 0;
-        double* yo = land ? a.y_out[oi] : nullptr;
-        double v[1] = {0.0};
+        R* yo = land ? a.y_out[oi] : nullptr;
+        int nzy = 0;
         FOR_CELLS(i) {
 #pragma unroll
           for (int c = 0; c < 4; ++c) {
             const size_t e = (size_t)c * ng + i;
-            double y = 0.0;
-            for (int j = 0; j < p; ++j) y = fma(sh.coef[KMAX + 2 + j], a.W[(size_t)j * n + e], y);
-            for (int r = 0; r < ncomb; ++r) y = fma(sh.coef[r], raw_slot(a, r)[e], y);
+            R y = R(0);
+            for (int j = 0; j < p; ++j) y = fma(shared_coef<R>(sh, KMAX + 2 + j), a.W[(size_t)j * n + e], y);
+            for (int r = 0; r < ncomb; ++r) y = fma(shared_coef<R>(sh, r), raw_slot(a, r)[e], y);
             a.W[e] = y;
             if (yo) yo[e] = y;
-            v[0] += (y != 0.0) ? 1.0 : 0.0;
+            nzy += (y != R(0)) ? 1 : 0;
           }
         }
+        double v[1] = {(double)nzy};
         auto post_y = [](volatile PhiCtrl* c) { c->wnz[0] = c->red[0] > 0.0; };
         if (!grid_reduce<1>(a, sh, v, PH_COMBINE, post_y)) goto finish;
         break;
@@ -681,20 +712,24 @@ finish:
 // Instantiations (block size, minimum resident blocks per SM for the register
 // budget).  The body adapts to blockDim.x; the taylor exponential needs at
 // least m_max + p + 1 = 69 threads.
-template <int NT, int MINB>
-__global__ void __launch_bounds__(NT, MINB) phi_kernel(const __grid_constant__ PhiArgs a) {
-  phi_body(a);
+template <typename R, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) phi_kernel(const __grid_constant__ PhiArgsT<R> a) {
+  phi_body<R>(a);
 }
 
 struct PhiVariant {
   const void* fn;
   int threads;
 };
-static const PhiVariant kVariants[] = {
-    {(const void*)phi_kernel<256, 2>, 256},
-    {(const void*)phi_kernel<192, 2>, 192},
-    {(const void*)phi_kernel<128, 3>, 128},
-    {(const void*)phi_kernel<96, 4>, 96},
+static const PhiVariant kVariants[2][4] = {
+    {{(const void*)phi_kernel<double, 256, 2>, 256},
+     {(const void*)phi_kernel<double, 192, 2>, 192},
+     {(const void*)phi_kernel<double, 128, 3>, 128},
+     {(const void*)phi_kernel<double, 96, 4>, 96}},
+    {{(const void*)phi_kernel<float, 256, 2>, 256},
+     {(const void*)phi_kernel<float, 192, 2>, 192},
+     {(const void*)phi_kernel<float, 128, 3>, 128},
+     {(const void*)phi_kernel<float, 96, 4>, 96}},
 };
 
 // Picks the instantiation and block count for a grid of ng cells.  The FP64
@@ -703,12 +738,12 @@ static const PhiVariant kVariants[] = {
 // (resident blocks) x (rounds of blockDim cells per block) x (warps per
 // block); the variant with the fewest such warp-rounds wins (ties: larger
 // blocks, fewer barriers participants).  Small grids use fewer blocks.
-int phi_select(int ng, PhiLaunch* out) {
+int phi_select(int ng, int single, PhiLaunch* out) {
   int dev = 0, nsm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return -1;
   if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -1;
   long long best = -1;
-  for (const PhiVariant& v : kVariants) {
+  for (const PhiVariant& v : kVariants[single ? 1 : 0]) {
     int per = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, v.fn, v.threads, 0) != cudaSuccess || per < 1)
       continue;
@@ -731,7 +766,8 @@ int phi_select(int ng, PhiLaunch* out) {
 }
 
 // Cooperative launch (all blocks co-resident: the grid barriers need it).
-int launch_phi_kernel(const PhiLaunch& L, const PhiArgs& a, cudaStream_t stream) {
+template <class A>
+int launch_phi_kernel(const PhiLaunch& L, const A& a, cudaStream_t stream) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(L.nblocks);
   cfg.blockDim = dim3(L.threads);
@@ -746,5 +782,7 @@ int launch_phi_kernel(const PhiLaunch& L, const PhiArgs& a, cudaStream_t stream)
   cudaError_t e = cudaLaunchKernelExC(&cfg, L.fn, args);
   return e == cudaSuccess ? 0 : (int)e;
 }
+template int launch_phi_kernel<PhiArgs>(const PhiLaunch&, const PhiArgs&, cudaStream_t);
+template int launch_phi_kernel<PhiArgsF>(const PhiLaunch&, const PhiArgsF&, cudaStream_t);
 
 }  // namespace swe

@@ -15,8 +15,9 @@
 #include "swe_dev.cuh"
 
 namespace swe {
-int launch_phi_kernel(const PhiLaunch& L, const PhiArgs& a, cudaStream_t stream);
-int phi_select(int ng, PhiLaunch* out);
+template <class A>
+int launch_phi_kernel(const PhiLaunch& L, const A& a, cudaStream_t stream);
+int phi_select(int ng, int single, PhiLaunch* out);
 }  // namespace swe
 
 using namespace swe;
@@ -69,7 +70,14 @@ struct swe_grid {
   DevAttempt* trace = nullptr;
   double* replay = nullptr;
   int replay_cap = 0;
-  PhiLaunch launch;          // persistent-kernel instantiation for this grid
+  PhiLaunch launch;          // persistent-kernel instantiation for this grid (FP64)
+  // mixed precision (created on first use)
+  TablesF TF;
+  void* dtabF = nullptr;
+  void* dwsF = nullptr;
+  PhiLaunch launchF;
+  float *VbufF = nullptr, *WF = nullptr, *tmpF = nullptr, *LringF = nullptr, *ZbufF = nullptr,
+        *auxF = nullptr, *ulinF = nullptr, *vinF = nullptr, *youtF = nullptr;
   size_t tab_bytes = 0;      // size of the table allocation
   // profiling (swe_profile_enable)
   bool prof_on = false;
@@ -94,7 +102,8 @@ namespace {
 // ---------------------------------------------------------------------------
 constexpr int TPB = 256;
 
-__global__ void k_aux(Tables T, const double* __restrict__ u, double* aux) {
+template <typename R>
+__global__ void k_aux(TablesT<R> T, const R* __restrict__ u, R* aux) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < T.ng; i += gridDim.x * blockDim.x)
     aux_cell(T, i, u, aux);
 }
@@ -131,6 +140,15 @@ __global__ void k_lincomb(size_t n, Comb cb, double* out) {
     for (int k = 0; k < cb.k; ++k) s = fma(cb.c[k], cb.x[k][e], s);
     out[e] = s;
   }
+}
+
+__global__ void k_d2f(size_t n, const double* __restrict__ x, float* y) {
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+    y[e] = (float)x[e];
+}
+__global__ void k_f2d(size_t n, const float* __restrict__ x, double* y) {
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+    y[e] = (double)x[e];
 }
 
 int grid_blocks(size_t work) {
@@ -264,7 +282,8 @@ int upload_grid(swe_grid* g) {
 int ensure_workspace(swe_grid* g) {
   if (!g->dtab) return fail(SWE_ERR_INVALID_ARG, "grid was built on the host only");
   if (g->dws) return SWE_OK;
-  if (phi_select(g->T.ng, &g->launch) != 0) return fail(SWE_ERR_CUDA, "occupancy query for phi kernel failed");
+  if (phi_select(g->T.ng, 0, &g->launch) != 0 || phi_select(g->T.ng, 1, &g->launchF) != 0)
+    return fail(SWE_ERR_CUDA, "occupancy query for phi kernel failed");
   const int nb = g->launch.nblocks;
   const size_t ng = g->T.ng, n = 4 * ng;
   size_t sizes[] = {
@@ -275,7 +294,7 @@ int ensure_workspace(swe_grid* g) {
       3 * n * 8,                   // Lring
       n * 8,                       // Zbuf
       4 * ng * 8,                  // aux
-      (size_t)nb * NRED * 8,       // part
+      (size_t)(nb > g->launchF.nblocks ? nb : g->launchF.nblocks) * NRED * 8,  // part
       (size_t)STAGE_VECS * n * 8,  // stage
       sizeof(PhiCtrl), sizeof(GridSync), sizeof(DevStats), (size_t)TRACE_CAP * sizeof(DevAttempt),
       sizeof(DevProfile)};
@@ -301,6 +320,60 @@ int ensure_workspace(swe_grid* g) {
   return SWE_OK;
 }
 
+// FP32 copies of the operator tables and the FP32 workspace of the mixed path.
+int ensure_mixed(swe_grid* g) {
+  if (g->dwsF) return SWE_OK;
+  const HostGrid& h = g->host;
+  const size_t ng = h.ng, n = 4 * ng;
+  std::vector<float> f;
+  auto conv = [&](const std::vector<double>& src) {
+    f.resize(src.size());
+    for (size_t k = 0; k < src.size(); ++k) f[k] = (float)src[k];
+  };
+  struct Part {
+    const std::vector<double>* src;
+    const float* __restrict__* dst;
+  };
+  std::vector<double> gdg(h.sdg.size());
+  for (size_t k = 0; k < gdg.size(); ++k) gdg[k] = h.ndd[k] - h.sdg[k];
+  TablesF& T = g->TF;
+  Part parts[] = {{&h.xyz, &T.nrm}, {&h.wl, &T.wl},   {&h.wld, &T.wld}, {&h.nc, &T.nc},
+                  {&h.ndd, &T.ndd}, {&gdg, &T.gdg},   {&h.vc, &T.vc},   {&h.vd, &T.vd}};
+  size_t total = 0;
+  for (auto& p : parts) total += (p.src->size() * 4 + 255) & ~size_t(255);
+  CK(cudaMalloc(&g->dtabF, total));
+  size_t off = 0;
+  for (auto& p : parts) {
+    conv(*p.src);
+    char* dst = (char*)g->dtabF + off;
+    CK(cudaMemcpy(dst, f.data(), f.size() * 4, cudaMemcpyHostToDevice));
+    *p.dst = (const float*)dst;
+    off += (p.src->size() * 4 + 255) & ~size_t(255);
+  }
+  T.ng = (int)ng;
+  T.nbr = g->T.nbr;
+  T.nu = (float)g->T.nu;
+  T.g = (float)g->T.g;
+  T.two_omega = (float)g->T.two_omega;
+  size_t sizes[] = {(size_t)(KMAX + 1) * n, (size_t)(PMAX + 1) * n, 8 * ng, 3 * n, n, 4 * ng, 4 * ng,
+                    (size_t)(PMAX + 1) * n, (size_t)NSMAX * n};
+  float** dst[] = {&g->VbufF, &g->WF, &g->tmpF, &g->LringF, &g->ZbufF, &g->auxF, &g->ulinF, &g->vinF, &g->youtF};
+  size_t tot = 0;
+  for (size_t s : sizes) tot += (s * 4 + 255) & ~size_t(255);
+  cudaError_t e = cudaMalloc(&g->dwsF, tot);
+  if (e != cudaSuccess) {
+    g->dwsF = nullptr;
+    return fail(SWE_ERR_NOMEM, std::string("mixed workspace allocation failed: ") + cudaGetErrorString(e));
+  }
+  char* p = (char*)g->dwsF;
+  for (int k = 0; k < 9; ++k) {
+    *dst[k] = (float*)p;
+    p += (sizes[k] * 4 + 255) & ~size_t(255);
+  }
+  CK(cudaMemset(g->dwsF, 0, tot));
+  return SWE_OK;
+}
+
 int resolve_opts(const phi_opts* in, phi_opts& o) {
   if (in)
     o = *in;
@@ -308,7 +381,8 @@ int resolve_opts(const phi_opts* in, phi_opts& o) {
     swe_phi_opts_default(&o);
   if (!(o.tol > 0.0) || o.m_init < 1 || o.m_max < 1 || o.m_max > KMAX || o.iom != 2 ||
       !(o.delta > 0.0) || !(o.gamma > 0.0) || !(o.kappa > 1.0) || o.max_reject < 0 ||
-      (o.tol_mode != 0 && o.tol_mode != 1) || (o.replay && o.n_replay < 1))
+      (o.tol_mode != 0 && o.tol_mode != 1) || (o.replay && o.n_replay < 1) ||
+      (o.precision != 0 && o.precision != 1))
     return fail(SWE_ERR_INVALID_ARG, "invalid phi_opts (m_max <= 64, iom == 2, tol > 0, kappa > 1)");
   return SWE_OK;
 }
@@ -326,26 +400,13 @@ int stage_replay(swe_grid* g, const phi_opts& o, cudaStream_t st) {
 }
 
 // One phipm_simul_iom2 evaluation; aux of u_lin must already be in g->aux.
-int phi_call(swe_grid* g, const double* u_lin, double dt, int p, const double* const* v, int ns,
-             const double* rho, double* const* y_out, const phi_opts& o, int call_index, int* m_slot,
-             int replay_offset, cudaStream_t st) {
-  PhiArgs a{};
-  a.T = g->T;
-  a.u_lin = u_lin;
-  a.aux = g->aux;
+template <class A>
+void fill_phi_args(swe_grid* g, A& a, double dt, int p, int ns, const double* rho, const phi_opts& o,
+                   int call_index, int* m_slot, int replay_offset) {
   a.dt = dt;
   a.p = p;
   a.ns = ns;
-  for (int i = 0; i < ns; ++i) {
-    a.rho[i] = rho[i];
-    a.y_out[i] = y_out[i];
-  }
-  for (int l = 0; l <= p; ++l) a.v[l] = v[l];
-  a.Vbuf = g->Vbuf;
-  a.W = g->W;
-  a.tmp = g->tmp;
-  a.Lring = g->Lring;
-  a.Zbuf = g->Zbuf;
+  for (int i = 0; i < ns; ++i) a.rho[i] = rho[i];
   a.part = g->part;
   a.ctrl = g->ctrl;
   a.sync = g->sync;
@@ -366,12 +427,83 @@ int phi_call(swe_grid* g, const double* u_lin, double dt, int p, const double* c
   a.max_reject = o.max_reject;
   a.nA = g->host.nA;
   a.prof = g->prof_on ? g->dprof : nullptr;
+}
+
+// Linearisation data of u_lin for the following phi calls: eta and n x u
+// (and, in the mixed path, the FP32 copy of u_lin).
+int prepare_lin(swe_grid* g, const double* u_lin, const phi_opts& o, cudaStream_t st) {
+  const int nb = grid_blocks(g->T.ng);
+  if (o.precision == 0) {
+    k_aux<double><<<nb, TPB, 0, st>>>(g->T, u_lin, g->aux);
+    CK(cudaGetLastError());
+    count_launches(g, 1);
+    return SWE_OK;
+  }
+  const size_t n = (size_t)4 * g->T.ng;
+  k_d2f<<<grid_blocks(n), TPB, 0, st>>>(n, u_lin, g->ulinF);
+  k_aux<float><<<nb, TPB, 0, st>>>(g->TF, g->ulinF, g->auxF);
+  CK(cudaGetLastError());
+  count_launches(g, 2);
+  return SWE_OK;
+}
+
+// One phipm_simul_iom2 evaluation; prepare_lin(u_lin) must precede it on the stream.
+int phi_call(swe_grid* g, const double* u_lin, double dt, int p, const double* const* v, int ns,
+             const double* rho, double* const* y_out, const phi_opts& o, int call_index, int* m_slot,
+             int replay_offset, cudaStream_t st) {
   CK(cudaMemsetAsync(g->sync, 0, sizeof(GridSync), st));
+  if (o.precision == 0) {
+    PhiArgs a{};
+    a.T = g->T;
+    a.u_lin = u_lin;
+    a.aux = g->aux;
+    for (int i = 0; i < ns; ++i) a.y_out[i] = y_out[i];
+    for (int l = 0; l <= p; ++l) a.v[l] = v[l];
+    a.Vbuf = g->Vbuf;
+    a.W = g->W;
+    a.tmp = g->tmp;
+    a.Lring = g->Lring;
+    a.Zbuf = g->Zbuf;
+    fill_phi_args(g, a, dt, p, ns, rho, o, call_index, m_slot, replay_offset);
+    ProfSpan span(g, st, &g->phi_ev);
+    int e = launch_phi_kernel(g->launch, a, st);
+    if (e != 0) return cuda_fail((cudaError_t)e, "cudaLaunchCooperativeKernel(phi_kernel)");
+    span.finish();
+    count_launches(g, 1);
+    return SWE_OK;
+  }
+  // mixed precision: FP32 copies of the inputs, FP32 outputs widened afterwards
+  const size_t n = (size_t)4 * g->T.ng;
+  PhiArgsF a{};
+  a.T = g->TF;
+  a.u_lin = g->ulinF;
+  a.aux = g->auxF;
+  for (int l = 0; l <= p; ++l) {
+    if (v[l]) {
+      k_d2f<<<grid_blocks(n), TPB, 0, st>>>(n, v[l], g->vinF + (size_t)l * n);
+      count_launches(g, 1);
+      a.v[l] = g->vinF + (size_t)l * n;
+    } else {
+      a.v[l] = nullptr;
+    }
+  }
+  for (int i = 0; i < ns; ++i) a.y_out[i] = g->youtF + (size_t)i * n;
+  a.Vbuf = g->VbufF;
+  a.W = g->WF;
+  a.tmp = g->tmpF;
+  a.Lring = g->LringF;
+  a.Zbuf = g->ZbufF;
+  fill_phi_args(g, a, dt, p, ns, rho, o, call_index, m_slot, replay_offset);
   ProfSpan span(g, st, &g->phi_ev);
-  int e = launch_phi_kernel(g->launch, a, st);
-  if (e != 0) return cuda_fail((cudaError_t)e, "cudaLaunchCooperativeKernel(phi_kernel)");
+  int e = launch_phi_kernel(g->launchF, a, st);
+  if (e != 0) return cuda_fail((cudaError_t)e, "cudaLaunchCooperativeKernel(phi_kernel<float>)");
   span.finish();
   count_launches(g, 1);
+  for (int i = 0; i < ns; ++i) {
+    k_f2d<<<grid_blocks(n), TPB, 0, st>>>(n, g->youtF + (size_t)i * n, y_out[i]);
+    count_launches(g, 1);
+  }
+  CK(cudaGetLastError());
   return SWE_OK;
 }
 
@@ -516,6 +648,8 @@ void swe_destroy_grid(swe_grid* g) {
   for (cudaEvent_t e : g->ev_pool) cudaEventDestroy(e);
   if (g->dtab) cudaFree(g->dtab);
   if (g->dws) cudaFree(g->dws);
+  if (g->dtabF) cudaFree(g->dtabF);
+  if (g->dwsF) cudaFree(g->dwsF);
   if (g->replay) cudaFree(g->replay);
   delete g;
 }
@@ -557,7 +691,7 @@ int swe_jv(const swe_grid* gc, const double* u, const double* x, double* jx, voi
   const Tables& T = g->T;
   cudaStream_t st = S(stream);
   int nb = grid_blocks(T.ng);
-  k_aux<<<nb, TPB, 0, st>>>(T, u, g->aux);
+  k_aux<double><<<nb, TPB, 0, st>>>(T, u, g->aux);
   k_pass1<MODE_J><<<nb, TPB, 0, st>>>(T, x, 1.0, u, g->tmp2);
   k_pass2<MODE_J><<<nb, TPB, 0, st>>>(T, x, 1.0, g->tmp2, g->aux, 1.0, jx);
   CK(cudaGetLastError());
@@ -576,11 +710,10 @@ int phi_action(swe_grid* g, const double* u_lin, double dt, int p, const double*
   if ((rc = ensure_workspace(g))) return rc;
   cudaStream_t st = S(stream);
   if ((rc = stage_replay(g, o, st))) return rc;
+  if (o.precision == 1 && (rc = ensure_mixed(g))) return rc;
   ProfSpan span(g, st, &g->call_ev);
   CK(cudaMemsetAsync(g->stats, 0, sizeof(DevStats), st));
-  k_aux<<<grid_blocks(g->T.ng), TPB, 0, st>>>(g->T, u_lin, g->aux);
-  CK(cudaGetLastError());
-  count_launches(g, 1);
+  if ((rc = prepare_lin(g, u_lin, o, st))) return rc;
   if ((rc = phi_call(g, u_lin, dt, p, v, ns, rho, y_out, o, 0, nullptr, 0, st))) return rc;
   span.finish();
   return read_stats(g, stats, st);
@@ -635,11 +768,10 @@ int exprb_step(swe_grid* g, int scheme, double dt, const double* u_n, double* u_
   double* B[STAGE_VECS];
   for (int k = 0; k < STAGE_VECS; ++k) B[k] = g->stage + (size_t)k * n;
   double* vF = B[0];
+  if (o.precision == 1 && (rc = ensure_mixed(g))) return rc;
   ProfSpan span(g, st, &g->call_ev);
   CK(cudaMemsetAsync(g->stats, 0, sizeof(DevStats), st));
-  k_aux<<<grid_blocks(g->T.ng), TPB, 0, st>>>(g->T, u_n, g->aux);
-  CK(cudaGetLastError());
-  count_launches(g, 1);
+  if ((rc = prepare_lin(g, u_n, o, st))) return rc;
   if ((rc = run_rhs(g, u_n, vF, dt, st))) return rc;  // v = dt F(u_n)
   int* slots = o.m_carry ? state->m_slots : nullptr;
   auto slot = [&](int k) { return slots ? slots + k : nullptr; };

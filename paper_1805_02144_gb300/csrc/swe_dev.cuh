@@ -1,5 +1,7 @@
 // Device-side building blocks: operator tables, the two-pass cell stencils of
 // F(u), J(u)x and the quadratic part Q(d), and bounded grid-wide barriers.
+// The stencils are templated on the real type R of tables, vectors and
+// arithmetic: double for the FP64 path, float for the mixed-precision path.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -8,37 +10,42 @@ namespace swe {
 
 constexpr int SLOTS = 6;
 
-// Operator tables of one grid (read-only for the lifetime of the grid).
-struct Tables {
+// Operator tables of one grid in precision R (read-only for the grid's life).
+template <typename R>
+struct TablesT {
   int ng;
-  double nu;      // dissipation coefficient of Eq. eq:niu
-  double g;       // gravity
-  double two_omega;
+  R nu;           // dissipation coefficient of Eq. eq:niu
+  R g;            // gravity
+  R two_omega;
   const int32_t* __restrict__ nbr;  // [6][ng]
-  const double* __restrict__ nrm;   // [3][ng] unit normals
-  const double* __restrict__ wl;    // [6][ng]
-  const double* __restrict__ wld;   // [ng]
-  const double* __restrict__ nc;    // [3][6][ng]
-  const double* __restrict__ ndd;   // [3][ng]
-  const double* __restrict__ gdg;   // [3][ng] G diagonal (ndd - sdg of the host tables)
-  const double* __restrict__ vc;    // [3][6][ng]
-  const double* __restrict__ vd;    // [3][ng]
+  const R* __restrict__ nrm;   // [3][ng] unit normals
+  const R* __restrict__ wl;    // [6][ng]
+  const R* __restrict__ wld;   // [ng]
+  const R* __restrict__ nc;    // [3][6][ng]
+  const R* __restrict__ ndd;   // [3][ng]
+  const R* __restrict__ gdg;   // [3][ng] G diagonal (ndd - sdg of the host tables)
+  const R* __restrict__ vc;    // [3][6][ng]
+  const R* __restrict__ vd;    // [3][ng]
 };
+using Tables = TablesT<double>;
+using TablesF = TablesT<float>;
 
-// Pass-1 outputs per cell, 8 planes of ng: [L x (4), scalar, vector (3)].
+// Pass-1 outputs per cell: 4 Laplacian planes and 4 scalar/vector planes.
 enum StencilMode { MODE_F = 0, MODE_J = 1, MODE_Q = 2 };
 
 // ---------------------------------------------------------------------------
 // Loads.  Data produced inside the same persistent launch must not go through
 // the non-coherent read-only path, so kernels that write what they later
 // gather read with plain loads (`ld`); inputs fixed for the whole launch use
-// __ldg.
+// __ldg.  Operator tables are read once per cell and pass: they bypass L1
+// allocation and are marked first to leave L2, so that L1 and L2 keep the
+// gathered vectors (written one phase earlier).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double ld(const double* p) { return *p; }
-__device__ __forceinline__ double ldro(const double* p) { return __ldg(p); }
-// Operator tables are read once per cell and pass: they bypass L1 allocation
-// and are marked first to leave L2, so that L1 and L2 keep the gathered
-// vectors (written one phase earlier).
+template <typename R>
+__device__ __forceinline__ R ld(const R* p) { return *p; }
+template <typename R>
+__device__ __forceinline__ R ldro(const R* p) { return __ldg(p); }
+
 __device__ __forceinline__ unsigned long long l2_evict_first_policy() {
   unsigned long long pol;
   asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
@@ -50,6 +57,12 @@ __device__ __forceinline__ double ldtab(const double* p) {
       : "=d"(v) : "l"(p), "l"(l2_evict_first_policy()));
   return v;
 }
+__device__ __forceinline__ float ldtab(const float* p) {
+  float v;
+  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.f32 %0, [%1], %2;"
+      : "=f"(v) : "l"(p), "l"(l2_evict_first_policy()));
+  return v;
+}
 __device__ __forceinline__ int ldtabi(const int32_t* p) {
   int v;
   asm("ld.global.nc.L1::no_allocate.L2::cache_hint.s32 %0, [%1], %2;"
@@ -58,15 +71,16 @@ __device__ __forceinline__ int ldtabi(const int32_t* p) {
 }
 
 // L psi at cell i for one plane: wld_i psi_i + sum_k wl_k psi_{nbr_k}
-__device__ __forceinline__ double lap_cell(const Tables& T, int i, const int (&nb)[SLOTS],
-                                           const double* psi) {
-  double acc = ldtab(T.wld + i) * ld(psi + i);
+template <typename R>
+__device__ __forceinline__ R lap_cell(const TablesT<R>& T, int i, const int (&nb)[SLOTS], const R* psi) {
+  R acc = ldtab(T.wld + i) * ld(psi + i);
 #pragma unroll
   for (int k = 0; k < SLOTS; ++k) acc = fma(ldtab(T.wl + (size_t)k * T.ng + i), ld(psi + nb[k]), acc);
   return acc;
 }
 
-__device__ __forceinline__ void load_nbr(const Tables& T, int i, int (&nb)[SLOTS]) {
+template <typename R>
+__device__ __forceinline__ void load_nbr(const TablesT<R>& T, int i, int (&nb)[SLOTS]) {
 #pragma unroll
   for (int k = 0; k < SLOTS; ++k) nb[k] = ldtabi(T.nbr + (size_t)k * T.ng + i);
 }
@@ -76,40 +90,37 @@ __device__ __forceinline__ void load_nbr(const Tables& T, int i, int (&nb)[SLOTS
 //   MODE_F: x = u.          L u (4), E = |u|^2/2 + g h, q = u h
 //   MODE_J: x = sx * xraw.  L x (4), s = u.x_u + g x_h,  q = x_u h + u x_h
 //   MODE_Q: x = d.          -,       E = |d_u|^2/2,      q = d_u d_h
-template <int MODE>
-__device__ __forceinline__ void pass1_cell(const Tables& T, int i, const double* x, double sx,
-                                           const double* u, double* Lout, double* sq) {
+template <int MODE, typename R>
+__device__ __forceinline__ void pass1_cell(const TablesT<R>& T, int i, const R* x, R sx, const R* u,
+                                           R* Lout, R* sq) {
   const int ng = T.ng;
   int nb[SLOTS];
   load_nbr(T, i, nb);
-  double xv[4];
+  R xv[4];
 #pragma unroll
   for (int c = 0; c < 4; ++c) xv[c] = ld(x + (size_t)c * ng + i);
   if (MODE != MODE_Q) {
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-      double lx = lap_cell(T, i, nb, x + (size_t)c * ng);
+      R lx = lap_cell(T, i, nb, x + (size_t)c * ng);
       Lout[(size_t)c * ng + i] = (MODE == MODE_J) ? sx * lx : lx;
     }
   }
   if (MODE == MODE_J) {
 #pragma unroll
     for (int c = 0; c < 4; ++c) xv[c] *= sx;
-    double uv[4];
+    R uv[4];
 #pragma unroll
     for (int c = 0; c < 4; ++c) uv[c] = ldro(u + (size_t)c * ng + i);
-    double s = fma(uv[0], xv[0], fma(uv[1], xv[1], fma(uv[2], xv[2], T.g * xv[3])));
-    sq[i] = s;
+    sq[i] = fma(uv[0], xv[0], fma(uv[1], xv[1], fma(uv[2], xv[2], T.g * xv[3])));
 #pragma unroll
     for (int c = 0; c < 3; ++c) sq[(size_t)(1 + c) * ng + i] = fma(xv[c], uv[3], uv[c] * xv[3]);
   } else if (MODE == MODE_F) {
-    double e = fma(0.5, fma(xv[0], xv[0], fma(xv[1], xv[1], xv[2] * xv[2])), T.g * xv[3]);
-    sq[i] = e;
+    sq[i] = fma(R(0.5), fma(xv[0], xv[0], fma(xv[1], xv[1], xv[2] * xv[2])), T.g * xv[3]);
 #pragma unroll
     for (int c = 0; c < 3; ++c) sq[(size_t)(1 + c) * ng + i] = xv[c] * xv[3];
   } else {
-    double e = 0.5 * fma(xv[0], xv[0], fma(xv[1], xv[1], xv[2] * xv[2]));
-    sq[i] = e;
+    sq[i] = R(0.5) * fma(xv[0], xv[0], fma(xv[1], xv[1], xv[2] * xv[2]));
 #pragma unroll
     for (int c = 0; c < 3; ++c) sq[(size_t)(1 + c) * ng + i] = xv[c] * xv[3];
   }
@@ -124,20 +135,19 @@ __device__ __forceinline__ void pass1_cell(const Tables& T, int i, const double*
 //   s', q' of z'                                      -> sq
 // and returns |z'|^2 of the cell.  No value of z' is gathered, so rnew may be
 // written while neighbours still read z.
-__device__ __forceinline__ double orth_pass1_cell(const Tables& T, int i, const double* z,
-                                                  const double* rj, const double* rm, double aj,
-                                                  double am, const double* Lj, const double* Lm,
-                                                  double* rnew, double* Lnew, const double* u,
-                                                  double* sq) {
+template <typename R>
+__device__ __forceinline__ R orth_pass1_cell(const TablesT<R>& T, int i, const R* z, const R* rj,
+                                             const R* rm, R aj, R am, const R* Lj, const R* Lm,
+                                             R* rnew, R* Lnew, const R* u, R* sq) {
   const int ng = T.ng;
   int nb[SLOTS];
   load_nbr(T, i, nb);
-  double zp[4], nrm = 0.0;
+  R zp[4], nrm = R(0);
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
     const size_t e = (size_t)c * ng + i;
-    double v = fma(-aj, ld(rj + e), ld(z + e));
-    double lz = fma(-aj, ld(Lj + e), lap_cell(T, i, nb, z + (size_t)c * ng));
+    R v = fma(-aj, ld(rj + e), ld(z + e));
+    R lz = fma(-aj, ld(Lj + e), lap_cell(T, i, nb, z + (size_t)c * ng));
     if (rm) {
       v = fma(-am, ld(rm + e), v);
       lz = fma(-am, ld(Lm + e), lz);
@@ -147,7 +157,7 @@ __device__ __forceinline__ double orth_pass1_cell(const Tables& T, int i, const 
     Lnew[e] = lz;
     nrm = fma(v, v, nrm);
   }
-  double uv[4];
+  R uv[4];
 #pragma unroll
   for (int c = 0; c < 4; ++c) uv[c] = ldro(u + (size_t)c * ng + i);
   sq[i] = fma(uv[0], zp[0], fma(uv[1], zp[1], fma(uv[2], zp[2], T.g * zp[3])));
@@ -161,15 +171,14 @@ __device__ __forceinline__ double orth_pass1_cell(const Tables& T, int i, const 
 //   Lp, sq: the planes pass 1 wrote (Laplacian, scalar + vector)
 //   aux (MODE_J only): [eta, P_x, P_y, P_z] of the linearisation state,
 //   eta = V u + f, P = n x u.
-template <int MODE>
-__device__ __forceinline__ void pass2_cell(const Tables& T, int i, const double* x, double sx,
-                                           const double* Lp, const double* sq, const double* aux,
-                                           double out[4]) {
+template <int MODE, typename R>
+__device__ __forceinline__ void pass2_cell(const TablesT<R>& T, int i, const R* x, R sx, const R* Lp,
+                                           const R* sq, const R* aux, R out[4]) {
   const int ng = T.ng;
   int nb[SLOTS];
   load_nbr(T, i, nb);
   // relative vorticity of x: V . x_u
-  double vor = 0.0;
+  R vor = R(0);
 #pragma unroll
   for (int c = 0; c < 3; ++c) vor = fma(ldtab(T.vd + (size_t)c * ng + i), ld(x + (size_t)c * ng + i), vor);
 #pragma unroll
@@ -179,52 +188,49 @@ __device__ __forceinline__ void pass2_cell(const Tables& T, int i, const double*
     for (int c = 0; c < 3; ++c)
       vor = fma(ldtab(T.vc + ((size_t)c * SLOTS + k) * ng + i), ld(x + (size_t)c * ng + j), vor);
   }
-  // raw gradient of the scalar plane and divergence of the vector planes
-  const double* sc = sq;
-  const double sci = ld(sc + i);
-  double gr[3], dv = 0.0;
+  // gradient of the scalar plane (before projection) and divergence of the vector planes
+  const R sci = ld(sq + i);
+  R gr[3], dv = R(0);
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    double nd = ldtab(T.ndd + (size_t)c * ng + i);
     gr[c] = ldtab(T.gdg + (size_t)c * ng + i) * sci;
-    dv = fma(nd, ld(sq + (size_t)(1 + c) * ng + i), dv);
+    dv = fma(ldtab(T.ndd + (size_t)c * ng + i), ld(sq + (size_t)(1 + c) * ng + i), dv);
   }
 #pragma unroll
   for (int k = 0; k < SLOTS; ++k) {
     const int j = nb[k];
-    const double scj = ld(sc + j);
+    const R scj = ld(sq + j);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      double w = ldtab(T.nc + ((size_t)c * SLOTS + k) * ng + i);
+      R w = ldtab(T.nc + ((size_t)c * SLOTS + k) * ng + i);
       gr[c] = fma(w, scj, gr[c]);
       dv = fma(w, ld(sq + (size_t)(1 + c) * ng + j), dv);
     }
   }
-  double n0 = ldtab(T.nrm + i), n1 = ldtab(T.nrm + ng + i), n2 = ldtab(T.nrm + 2 * (size_t)ng + i);
-  double ng_ = fma(n0, gr[0], fma(n1, gr[1], n2 * gr[2]));
-  gr[0] = fma(-n0, ng_, gr[0]);
-  gr[1] = fma(-n1, ng_, gr[1]);
-  gr[2] = fma(-n2, ng_, gr[2]);
-  // own values of x (scaled)
-  double xo[3];
+  R n0 = ldtab(T.nrm + i), n1 = ldtab(T.nrm + ng + i), n2 = ldtab(T.nrm + 2 * (size_t)ng + i);
+  R ngr = fma(n0, gr[0], fma(n1, gr[1], n2 * gr[2]));
+  gr[0] = fma(-n0, ngr, gr[0]);
+  gr[1] = fma(-n1, ngr, gr[1]);
+  gr[2] = fma(-n2, ngr, gr[2]);
+  R xo[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) xo[c] = ld(x + (size_t)c * ng + i);
-  double nx0 = n1 * xo[2] - n2 * xo[1];
-  double nx1 = n2 * xo[0] - n0 * xo[2];
-  double nx2 = n0 * xo[1] - n1 * xo[0];
+  R nx0 = n1 * xo[2] - n2 * xo[1];
+  R nx1 = n2 * xo[0] - n0 * xo[2];
+  R nx2 = n0 * xo[1] - n1 * xo[0];
   if (MODE == MODE_J) {
     vor *= sx;
     nx0 *= sx;
     nx1 *= sx;
     nx2 *= sx;
-    double eta = ld(aux + i);
-    double p0 = ld(aux + (size_t)ng + i), p1 = ld(aux + 2 * (size_t)ng + i), p2 = ld(aux + 3 * (size_t)ng + i);
+    R eta = ld(aux + i);
+    R p0 = ld(aux + (size_t)ng + i), p1 = ld(aux + 2 * (size_t)ng + i), p2 = ld(aux + 3 * (size_t)ng + i);
     out[0] = -fma(vor, p0, fma(eta, nx0, gr[0]));
     out[1] = -fma(vor, p1, fma(eta, nx1, gr[1]));
     out[2] = -fma(vor, p2, fma(eta, nx2, gr[2]));
     out[3] = -dv;
   } else if (MODE == MODE_F) {
-    double eta = fma(T.two_omega, n2, vor);
+    R eta = fma(T.two_omega, n2, vor);
     out[0] = -fma(eta, nx0, gr[0]);
     out[1] = -fma(eta, nx1, gr[1]);
     out[2] = -fma(eta, nx2, gr[2]);
@@ -242,20 +248,21 @@ __device__ __forceinline__ void pass2_cell(const Tables& T, int i, const double*
 }
 
 // aux = [eta, n x u] of a linearisation state u at cell i.
-__device__ __forceinline__ void aux_cell(const Tables& T, int i, const double* u, double* aux) {
+template <typename R>
+__device__ __forceinline__ void aux_cell(const TablesT<R>& T, int i, const R* u, R* aux) {
   const int ng = T.ng;
   int nb[SLOTS];
   load_nbr(T, i, nb);
-  double vor = 0.0;
+  R vor = R(0);
 #pragma unroll
-  for (int c = 0; c < 3; ++c) vor = fma(ldro(T.vd + (size_t)c * ng + i), ldro(u + (size_t)c * ng + i), vor);
+  for (int c = 0; c < 3; ++c) vor = fma(ldtab(T.vd + (size_t)c * ng + i), ldro(u + (size_t)c * ng + i), vor);
 #pragma unroll
   for (int k = 0; k < SLOTS; ++k)
 #pragma unroll
     for (int c = 0; c < 3; ++c)
-      vor = fma(ldro(T.vc + ((size_t)c * SLOTS + k) * ng + i), ldro(u + (size_t)c * ng + nb[k]), vor);
-  double n0 = ldro(T.nrm + i), n1 = ldro(T.nrm + ng + i), n2 = ldro(T.nrm + 2 * (size_t)ng + i);
-  double u0 = ldro(u + i), u1 = ldro(u + ng + i), u2 = ldro(u + 2 * (size_t)ng + i);
+      vor = fma(ldtab(T.vc + ((size_t)c * SLOTS + k) * ng + i), ldro(u + (size_t)c * ng + nb[k]), vor);
+  R n0 = ldtab(T.nrm + i), n1 = ldtab(T.nrm + ng + i), n2 = ldtab(T.nrm + 2 * (size_t)ng + i);
+  R u0 = ldro(u + i), u1 = ldro(u + ng + i), u2 = ldro(u + 2 * (size_t)ng + i);
   aux[i] = fma(T.two_omega, n2, vor);
   aux[(size_t)ng + i] = n1 * u2 - n2 * u1;
   aux[2 * (size_t)ng + i] = n2 * u0 - n0 * u2;

@@ -1,0 +1,87 @@
+"""GPU parity of the mixed-precision path (phi_opts.precision = 1).
+
+FP32 operator tables, stencils and Krylov basis; FP64 reductions, control,
+exponential, F(u_n), D_ni and state update; Tol = 1e-6 (relative).  The
+target is the FP64 oracle within 1e-5 relative L2 in h and in the stacked
+velocity.  The 24-step level-8 run (12 h at dt = 1800 s) is compared with the
+FP64 GPU path, which the FP64 parity tests tie to the oracle within 1e-10;
+the oracle itself is compared directly on level 5 (24 steps) and level 8
+(2 steps).
+"""
+import numpy as np
+import pytest
+
+from oracle.phipm import PhiOpts, phipm_simul_iom2
+from oracle.schemes import KrylovPhi, integrate
+from paper_1805_02144_gb300.inputs import balanced_state, random_vector
+from parity_utils import dev, host, pair, rel_l2_parts, to_oracle, to_prod
+
+pytestmark = pytest.mark.gpu
+
+MIXED = {"precision": 1, "tol": 1e-6}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1805_02144_gb300 import build
+    build.build()
+
+
+def test_mixed_phi_action_matches_oracle():
+    from paper_1805_02144_gb300.api import phi_action
+    G, s, idx = pair(5)
+    u = balanced_state(s.grid.x, 3, 400.0)
+    dt = 1800.0
+    v = [None, dt * s.F(u), None, random_vector(s.n, 7) * 1e-3, random_vector(s.n, 8) * 1e-3]
+    W, _ = phipm_simul_iom2(lambda x: dt * s.Jv(u, x), [0.5, 1.0], v, PhiOpts(tol=1e-10), s.nA)
+    outs, st = phi_action(G, dev(to_prod(u, idx)), dt, [None if x is None else dev(to_prod(x, idx)) for x in v],
+                          [0.5, 1.0], opts=MIXED, stats=True)
+    assert st["status"] == 0
+    for w_ref, o in zip(W, outs):
+        got = to_oracle(host(o), idx)
+        assert np.linalg.norm(got - w_ref) <= 1e-5 * np.linalg.norm(w_ref)
+
+
+def _run(G, u0p, scheme, dt, nsteps, opts):
+    from paper_1805_02144_gb300.api import SchemeState, exprb_step
+    st = SchemeState(G)
+    u = dev(u0p)
+    for _ in range(nsteps):
+        u, info = exprb_step(G, scheme, dt, u, state=st, opts=opts, stats=True)
+        assert info["status"] == 0
+    return host(u)
+
+
+def test_mixed_exprb53_level5_12h_matches_oracle():
+    G, s, idx = pair(5)
+    u0 = balanced_state(s.grid.x, 3, 400.0)
+    ref = integrate("exprb53", s, u0, 1800.0, 24, KrylovPhi(s, PhiOpts(tol=1e-8)))
+    got = to_oracle(_run(G, to_prod(u0, idx), "exprb53", 1800.0, 24, MIXED), idx)
+    eh, ev = rel_l2_parts(got, ref, s.ng)
+    assert eh <= 1e-5 and ev <= 1e-5, (eh, ev)
+
+
+def test_mixed_exprb53_level8_two_steps_match_oracle():
+    G, s, idx = pair(8)
+    u0 = balanced_state(s.grid.x, 3, 400.0)
+    ref = integrate("exprb53", s, u0, 1800.0, 2, KrylovPhi(s, PhiOpts(tol=1e-8)))
+    got = to_oracle(_run(G, to_prod(u0, idx), "exprb53", 1800.0, 2, MIXED), idx)
+    eh, ev = rel_l2_parts(got, ref, s.ng)
+    assert eh <= 1e-5 and ev <= 1e-5, (eh, ev)
+
+
+def test_mixed_exprb53_level8_12h_matches_fp64_path():
+    """The full precision workload: level 8, dt = 1800 s, 12 h."""
+    from paper_1805_02144_gb300.api import Grid
+    G = Grid(8)
+    u0 = balanced_state(G.cell_centres(), 3, 400.0)
+    a = _run(G, u0, "exprb53", 1800.0, 24, MIXED)
+    b = _run(G, u0, "exprb53", 1800.0, 24, {"tol": 1e-8})
+    eh, ev = rel_l2_parts(a, b, G.ncells)
+    assert eh <= 1e-5 and ev <= 1e-5, (eh, ev)
+    area = G.cell_areas()
+    m0, m1 = np.sum(area * u0[3 * G.ncells:]), np.sum(area * a[3 * G.ncells:])
+    assert abs(m1 - m0) <= 1e-6 * m0
