@@ -194,10 +194,11 @@ int exprb_step(swe_grid* grid, int scheme, double dt, const double* u_n, double*
 /* Opt-in timing and operation counts (CUDA events recorded on the call's
  * stream around every persistent phi launch and every exprb_step / phi_action
  * call; counters of IOM2 iterations, w_j products and combination terms kept
- * on the device).  phi_flop is the FP64 operation count of the phi launches
- * (per cell: 342 per IOM2 iteration, 310 per w_j product, 8 per combination
- * term); phi_bytes the algorithmic vector bytes (per cell: 136 per IOM2
- * iteration, 104 per w_j product, 32 per combination term), operator tables
+ * on the device).  phi_flop is the operation count of the phi launches (per
+ * cell: 342 per IOM2 iteration, 310 per w_j product, 8 per combination term;
+ * FP64 or FP32 by the launch's precision); phi_bytes the algorithmic vector
+ * bytes (per cell with FP64 vectors: 136 per IOM2 iteration, 104 per w_j
+ * product, 32 per combination term; half with FP32 vectors), operator tables
  * excluded. */
 typedef struct {
   double phi_ms;          /* summed duration of the persistent phi launches  */
@@ -218,6 +219,38 @@ typedef struct {
 int swe_profile_enable(swe_grid* grid, int on);
 /* Waits for `stream`, then fills *out with the totals since enabling. */
 int swe_profile_read(swe_grid* grid, swe_profile* out, void* stream);
+
+/* Ensembles (batching): nmem independent exprb42 trajectories, member m on
+ * grids[m] (grids may repeat and may differ in level) with step dt[m] and
+ * nsteps[m] steps per run, advanced together by ONE persistent cooperative
+ * launch per run: the launch's blocks are split into one group per member,
+ * each group runs its member's whole trajectory (F, both phipm_simul_iom2
+ * calls of Sec. 4.4, D_n2, update) with its own grid barrier, control block
+ * and Krylov workspace.  Member states are library-owned device buffers
+ * (n_m doubles, grid order); set/get copy device to device.  A run enqueues
+ * two memsets and one kernel and allocates nothing, so it can be captured in
+ * a CUDA graph.  The block split starts from a work model (cells x 2^level x
+ * simulated time) and swe_ensemble_tune re-splits it from measured group
+ * times (it runs the ensemble `rounds` times and restores the states and the
+ * carried Krylov sizes).  Each member carries its last accepted Krylov size
+ * per call from step to step and from run to run (m carry);
+ * swe_ensemble_reset clears it, as for a new trajectory.
+ * opts: FP64 only (precision 0), no replay.  All grids must be device grids
+ * on the current device. */
+typedef struct swe_ensemble swe_ensemble;
+int swe_ensemble_create(swe_grid* const* grids, int nmem, const double* dt, const int* nsteps,
+                        const phi_opts* opts, swe_ensemble** out);
+void swe_ensemble_destroy(swe_ensemble* ens);
+int swe_ensemble_set_state(swe_ensemble* ens, int m, const double* u, void* stream);
+int swe_ensemble_get_state(swe_ensemble* ens, int m, double* u, void* stream);
+int swe_ensemble_run(swe_ensemble* ens, void* stream);
+int swe_ensemble_reset(swe_ensemble* ens, void* stream);
+int swe_ensemble_tune(swe_ensemble* ens, int rounds, void* stream);
+/* Waits for `stream`; per-member statistics of the last run (array of nmem,
+ * or NULL; trace not filled), each member's group time in ms (or NULL) and
+ * its block count (or NULL). */
+int swe_ensemble_stats(swe_ensemble* ens, phi_stats* stats, double* member_ms, int* member_blocks,
+                       void* stream);
 
 /* Waits for `stream` and returns the first device-side error of the grid's
  * last phi_action / exprb_step (SWE_OK if none), clearing it. */

@@ -25,7 +25,9 @@ EXPORTS = ["swe_phi_opts_default", "swe_create_grid", "swe_create_grid_host", "s
            "phi_action",
            "swe_scheme_state_create", "swe_scheme_state_reset", "swe_scheme_state_destroy",
            "exprb_step", "swe_profile_enable", "swe_profile_read", "swe_device_status",
-           "swe_last_error"]
+           "swe_last_error", "swe_ensemble_create", "swe_ensemble_destroy", "swe_ensemble_set_state",
+           "swe_ensemble_get_state", "swe_ensemble_run", "swe_ensemble_reset", "swe_ensemble_tune",
+           "swe_ensemble_stats"]
 
 
 class PhiOptsC(C.Structure):
@@ -102,12 +104,24 @@ def load(path: Optional[str] = None) -> C.CDLL:
     L.swe_profile_enable.argtypes = [vp, C.c_int]
     L.swe_profile_read.argtypes = [vp, C.POINTER(ProfileC), vp]
     L.swe_device_status.argtypes = [vp, vp]
+    L.swe_ensemble_create.argtypes = [C.POINTER(vp), C.c_int, dp, C.POINTER(C.c_int),
+                                      C.POINTER(PhiOptsC), C.POINTER(vp)]
+    L.swe_ensemble_destroy.argtypes = [vp]
+    L.swe_ensemble_destroy.restype = None
+    L.swe_ensemble_set_state.argtypes = [vp, C.c_int, vp, vp]
+    L.swe_ensemble_get_state.argtypes = [vp, C.c_int, vp, vp]
+    L.swe_ensemble_run.argtypes = [vp, vp]
+    L.swe_ensemble_reset.argtypes = [vp, vp]
+    L.swe_ensemble_tune.argtypes = [vp, C.c_int, vp]
+    L.swe_ensemble_stats.argtypes = [vp, C.POINTER(PhiStatsC), dp, C.POINTER(C.c_int), vp]
     L.swe_last_error.argtypes = []
     L.swe_last_error.restype = C.c_char_p
     for name in ("swe_create_grid", "swe_create_grid_host", "swe_grid_export", "swe_grid_query", "swe_grid_cell_centres", "swe_grid_cell_areas",
                  "swe_rhs", "swe_jv", "swe_jv_noalloc", "phi_action", "swe_scheme_state_create",
                  "swe_scheme_state_reset", "exprb_step", "swe_device_status", "swe_profile_enable",
-                 "swe_profile_read"):
+                 "swe_profile_read", "swe_ensemble_create", "swe_ensemble_set_state",
+                 "swe_ensemble_get_state", "swe_ensemble_run", "swe_ensemble_reset", "swe_ensemble_tune",
+                 "swe_ensemble_stats"):
         getattr(L, name).restype = C.c_int
     _LIB = L
     return L

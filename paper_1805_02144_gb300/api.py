@@ -219,3 +219,59 @@ def swe_profile_read(grid: Grid, stream=None) -> dict:
              "decide_tail", "combine", "taylor", "decide_head"]
     d["phase_ms"] = {n: pr.phase_ms[i] for i, n in enumerate(names)}
     return d
+
+
+class Ensemble:
+    """swe_ensemble: independent exprb42 trajectories advanced by one persistent launch."""
+
+    def __init__(self, grids: Sequence[Grid], dt: Sequence[float], nsteps: Sequence[int], opts=None):
+        L = load()
+        nm = len(grids)
+        gh = (C.c_void_p * nm)(*[g.handle for g in grids])
+        dts = (C.c_double * nm)(*[float(x) for x in dt])
+        ns = (C.c_int * nm)(*[int(x) for x in nsteps])
+        o, keep = _opts(opts)
+        h = C.c_void_p()
+        check(L.swe_ensemble_create(gh, nm, dts, ns, C.byref(o), C.byref(h)))
+        del keep
+        self.handle = h
+        self.grids = list(grids)
+        self.nmem = nm
+
+    def set_state(self, m: int, u: torch.Tensor, stream=None) -> None:
+        check(load().swe_ensemble_set_state(self.handle, m, _ptr(u, self.grids[m].n, "u"), _stream(stream)))
+
+    def get_state(self, m: int, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+        out = _new(self.grids[m]) if out is None else out
+        check(load().swe_ensemble_get_state(self.handle, m, _ptr(out, self.grids[m].n, "out"), _stream(stream)))
+        return out
+
+    def run(self, stream=None) -> None:
+        check(load().swe_ensemble_run(self.handle, _stream(stream)))
+
+    def reset(self, stream=None) -> None:
+        """Forget the Krylov sizes carried from earlier steps (new trajectories)."""
+        check(load().swe_ensemble_reset(self.handle, _stream(stream)))
+
+    def tune(self, rounds: int = 2, stream=None) -> None:
+        check(load().swe_ensemble_tune(self.handle, rounds, _stream(stream)))
+
+    def stats(self, stream=None) -> dict:
+        nm = self.nmem
+        st = (PhiStatsC * nm)()
+        ms = (C.c_double * nm)()
+        nb = (C.c_int * nm)()
+        check(load().swe_ensemble_stats(self.handle, st, ms, nb, _stream(stream)))
+        return {"status": [st[i].status for i in range(nm)], "n_jv": [st[i].n_jv for i in range(nm)],
+                "member_ms": [ms[i] for i in range(nm)], "blocks": [nb[i] for i in range(nm)]}
+
+    def close(self) -> None:
+        if self.handle:
+            load().swe_ensemble_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

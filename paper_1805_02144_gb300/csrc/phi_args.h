@@ -20,6 +20,7 @@ struct DevStats {
 struct DevProfile {
   long long iters, wjv, comb_terms, launches;
   long long phase_ns[10];  // block 0's time per phase class (see phi_kernel.cu)
+  double flop, bytes;      // algorithmic operation count and vector bytes of the launches
 };
 
 // One trace record, the same layout as the public phi_attempt.
@@ -90,5 +91,24 @@ struct PhiArgsT {
 };
 using PhiArgs = PhiArgsT<double>;
 using PhiArgsF = PhiArgsT<float>;
+
+// One member of an ensemble launch: an exprb42 trajectory (Eq. eq3.11 with
+// the two phipm_simul_iom2 calls of Sec. 4.4) advanced nsteps steps by the
+// group of blocks [b0, b0 + nb).
+struct EnsMember {
+  PhiArgs c1;               // p = 1, rho = {3/4}: Y(3/4) = U_n2 - u_n  -> y1
+  PhiArgs c2;               // p = 3, rho = {1}, v_1 = dt F, v_3 = (32/9) dt D_n2 -> w
+  double* u;                // state (library-owned), n values
+  double* vF;               // dt F(u_n)
+  double* v3;               // (32/9) dt D_n2
+  double* y1;               // = c1.y_out[0]
+  double* w;                // = c2.y_out[0]
+  double* tmpS;             // 8 planes for the F and Q passes
+  double* aux;              // = c1.aux (written here)
+  double dt;
+  int nsteps;
+  int b0, nb;
+  unsigned long long t0, t1;  // globaltimer at the group's start and end (block 0)
+};
 
 }  // namespace swe

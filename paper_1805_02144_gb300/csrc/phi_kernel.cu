@@ -76,6 +76,7 @@ enum Phase { PH_PROLOGUE = 0, PH_W_PASS1, PH_W_PASS2, PH_K_PASS1, PH_K_PASS2, PH
              PH_TAYLOR, PH_CONTROL };
 
 struct Shared {
+  int gb, gn;  // this block's index in its group of co-operating blocks, group size
   unsigned long long t_last;
   double red[(PHI_MAX_THREADS / 32) * NRED];
   double coef[KMAX + PMAX + 4];
@@ -92,7 +93,7 @@ struct Shared {
 
 template <class A>
 __device__ __forceinline__ void phase_tick(const A& a, Shared& sh, int phase) {
-  if (a.prof && blockIdx.x == 0 && threadIdx.x == 0) {
+  if (a.prof && sh.gb == 0 && threadIdx.x == 0) {
     unsigned long long now = globaltimer();
     a.prof->phase_ns[phase] += (long long)(now - sh.t_last);
     sh.t_last = now;
@@ -106,7 +107,7 @@ __device__ bool grid_barrier(const A& a, Shared& sh, int phase) {
   __syncthreads();
   if (threadIdx.x == 0) {
     bool last;
-    unsigned int gen = bar_arrive(a.sync, gridDim.x, &last);
+    unsigned int gen = bar_arrive(a.sync, sh.gn, &last);
     bool ok = true;
     if (last)
       bar_release(a.sync, gen);
@@ -126,9 +127,9 @@ template <int K, class A, class Post>
 __device__ bool grid_reduce(const A& a, Shared& sh, double (&v)[K], int phase, Post post) {
   block_sum<K>(v, sh.red);
   if (threadIdx.x == 0) {
-    for (int k = 0; k < K; ++k) a.part[(size_t)blockIdx.x * NRED + k] = v[k];
+    for (int k = 0; k < K; ++k) a.part[(size_t)sh.gb * NRED + k] = v[k];
     bool last;
-    sh.gen = bar_arrive(a.sync, gridDim.x, &last);
+    sh.gen = bar_arrive(a.sync, sh.gn, &last);
     sh.last = last;
   }
   __syncthreads();
@@ -137,7 +138,7 @@ __device__ bool grid_reduce(const A& a, Shared& sh, double (&v)[K], int phase, P
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       double s = 0.0;
-      for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) s += a.part[(size_t)b * NRED + k];
+      for (int b = threadIdx.x; b < sh.gn; b += blockDim.x) s += a.part[(size_t)b * NRED + k];
       tot[k] = s;
     }
     block_sum<K>(tot, sh.red);
@@ -430,9 +431,11 @@ __device__ __forceinline__ double shared_coef<double>(const Shared& sh, int r) {
 template <>
 __device__ __forceinline__ float shared_coef<float>(const Shared& sh, int r) { return sh.coeff[r]; }
 
+// Algorithm 1 for one call, executed by the sh.gn blocks of a group.  Returns
+// false when the launch is being aborted (every block of the group returns
+// at the same barrier or at the next one).
 template <typename R>
-__device__ __forceinline__ void phi_body(const PhiArgsT<R>& a) {
-  __shared__ Shared sh;
+__device__ bool phi_run(const PhiArgsT<R>& a, Shared& sh) {
   const TablesT<R>& T = a.T;
   // happy-breakdown threshold relative to the window coefficients: near the
   // rounding floor of the basis precision
@@ -440,14 +443,14 @@ __device__ __forceinline__ void phi_body(const PhiArgsT<R>& a) {
   const int ng = T.ng;
   const size_t n = (size_t)4 * ng;
   const int p = a.p;
-  const int chunk = (ng + gridDim.x - 1) / gridDim.x;
-  const Range RG{min(ng, (int)blockIdx.x * chunk), min(ng, ((int)blockIdx.x + 1) * chunk)};
+  const int chunk = (ng + sh.gn - 1) / sh.gn;
+  const Range RG{min(ng, sh.gb * chunk), min(ng, (sh.gb + 1) * chunk)};
   const CellLoop CL(RG);
   PhiCtrl* C = a.ctrl;
 
   // ---- prologue: y = v_0, norms of the inputs -----------------------------
   if (threadIdx.x == 0) sh.t_last = globaltimer();
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (sh.gb == 0 && threadIdx.x == 0) {
     C->status = SWE_OK;
     C->n_jv = C->n_sub = C->n_rej = C->m_last = C->m_max_used = 0;
     C->replay_pos = 0;
@@ -456,23 +459,29 @@ __device__ __forceinline__ void phi_body(const PhiArgsT<R>& a) {
     C->n_iter = C->n_wjv = C->comb_terms = 0;
   }
   {
-    double v[NRED];
+    int nz0 = 0;
+    R sq[PMAX + 1];
 #pragma unroll
-    for (int k = 0; k < NRED; ++k) v[k] = 0.0;
+    for (int l = 0; l <= PMAX; ++l) sq[l] = R(0);
     FOR_CELLS(i) {
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
         const size_t e = (size_t)c * ng + i;
-        R yv0 = a.v[0] ? __ldg(a.v[0] + e) : R(0);
+        R yv0 = a.v[0] ? ld(a.v[0] + e) : R(0);
         a.W[e] = yv0;
-        v[0] += (yv0 != R(0)) ? 1.0 : 0.0;
+        nz0 += (yv0 != R(0)) ? 1 : 0;
         for (int l = 0; l <= p; ++l)
           if (a.v[l]) {
-            double x = (double)__ldg(a.v[l] + e);
-            v[1 + l] = fma(x, x, v[1 + l]);
+            R x = ld(a.v[l] + e);
+            sq[l] = fma(x, x, sq[l]);
           }
       }
     }
+    double v[NRED];
+#pragma unroll
+    for (int k = 0; k < NRED; ++k) v[k] = 0.0;
+    v[0] = (double)nz0;
+    for (int l = 0; l <= p; ++l) v[1 + l] = (double)sq[l];
     const int pp = p, tol_mode = a.tol_mode, m_max = a.m_max;
     const double rho0 = a.rho[0];
     const int m_init = (a.m_slot && *a.m_slot > 0) ? *a.m_slot : a.m_init;
@@ -488,18 +497,19 @@ __device__ __forceinline__ void phi_body(const PhiArgsT<R>& a) {
       c->done = (scale == 0.0) || !isfinite(scale);
       if (!isfinite(scale)) c->status = SWE_ERR_NONFINITE;
     };
-    if (!grid_reduce<NRED>(a, sh, v, PH_PROLOGUE, post)) goto finish;
+    if (!grid_reduce<NRED>(a, sh, v, PH_PROLOGUE, post)) return false;
   }
-  if (vldi(&C->done)) {
+  if (vldi(&C->done)) {  // all inputs zero (or non-finite): zero outputs
     for (int o = 0; o < a.ns; ++o)
       FOR_CELLS(i)
         for (int c = 0; c < 4; ++c) a.y_out[o][(size_t)c * ng + i] = R(0);
-    goto finish;
+    if (!grid_barrier(a, sh, PH_COMBINE)) return false;
+    return vldi(&C->status) == SWE_OK;
   }
 
   for (int oi = 0; oi < a.ns; ++oi) {
     const double t_out = a.rho[oi];
-    if (blockIdx.x == 0 && threadIdx.x == 0) C->t_out = t_out;
+    if (sh.gb == 0 && threadIdx.x == 0) C->t_out = t_out;
     while (vld(&C->t) < t_out) {
       // ---- step 1: w_j = A w_{j-1} + sum_l t^l/l! v_{j+l}  (Eq. eq3.18) ----
       const double t = vld(&C->t);
@@ -521,7 +531,7 @@ __device__ __forceinline__ void phi_body(const PhiArgsT<R>& a) {
         if (nz_prev) {
           FOR_CELLS(i)
             pass1_cell<MODE_J>(T, i, wprev, R(1), a.u_lin, a.tmp, a.tmp + (size_t)4 * ng);
-          if (!grid_barrier(a, sh, PH_W_PASS1)) goto finish;
+          if (!grid_barrier(a, sh, PH_W_PASS1)) return false;
         }
         R clr[PMAX + 1];
         for (int l = 0; l <= p - j; ++l) clr[l] = (R)cl[l];
@@ -536,7 +546,7 @@ __device__ __forceinline__ void phi_body(const PhiArgsT<R>& a) {
             const size_t e = (size_t)c * ng + i;
             R w = dtr * o[c];
             for (int l = 0; l <= p - j; ++l)
-              if (a.v[j + l]) w = fma(clr[l], __ldg(a.v[j + l] + e), w);
+              if (a.v[j + l]) w = fma(clr[l], ld(a.v[j + l] + e), w);
             wj[e] = w;
             nzc += (w != R(0)) ? 1 : 0;
             sqs = fma(w, w, sqs);
@@ -562,7 +572,7 @@ __device__ __forceinline__ void phi_body(const PhiArgsT<R>& a) {
             }
           }
         };
-        if (!grid_reduce<2>(a, sh, v, PH_W_PASS2, post)) goto finish;
+        if (!grid_reduce<2>(a, sh, v, PH_W_PASS2, post)) return false;
       }
 
       // ---- attempts on this substep ---------------------------------------
@@ -595,7 +605,7 @@ __device__ __forceinline__ void phi_body(const PhiArgsT<R>& a) {
             if (j == 0) {
               FOR_CELLS(i)
                 pass1_cell<MODE_J>(T, i, rj, R(1), a.u_lin, Lj, SQ);
-              if (!grid_barrier(a, sh, PH_K_PASS1)) goto finish;
+              if (!grid_barrier(a, sh, PH_K_PASS1)) return false;
             }
             const R zs = (R)(a.dt * sj);
             R d0 = R(0), d1 = R(0);
@@ -616,7 +626,7 @@ __device__ __forceinline__ void phi_body(const PhiArgsT<R>& a) {
               if (j > 0) c->hu[j - 1] = c->sig[j - 1] * c->red[0];
               c->hd[j] = c->sig[j] * c->red[1];
             };
-            if (!grid_reduce<2>(a, sh, v, PH_K_PASS2, post_dots)) goto finish;
+            if (!grid_reduce<2>(a, sh, v, PH_K_PASS2, post_dots)) return false;
             // z' = z - h_{j-1,j} v_{j-1} - h_{j,j} v_j with its pass-1 planes
             const R am = j > 0 ? (R)(vld(&C->hu[j - 1]) * vld(&C->sig[j - 1])) : R(0);
             const R aj = (R)(vld(&C->hd[j]) * sj);
@@ -645,12 +655,12 @@ __device__ __forceinline__ void phi_body(const PhiArgsT<R>& a) {
                 c->sig[j + 1] = 1.0 / hn;
               }
             };
-            if (!grid_reduce<1>(a, sh, w, PH_ORTH, post_norm)) goto finish;
+            if (!grid_reduce<1>(a, sh, w, PH_ORTH, post_norm)) return false;
           }
         }
         // ---- exponential, error estimate, controller (steps 2(ii)-6) -------
-        if (blockIdx.x == 0) decide(a, sh);
-        if (!grid_barrier(a, sh, PH_DECIDE)) goto finish;
+        if (sh.gb == 0) decide(a, sh);
+        if (!grid_barrier(a, sh, PH_DECIDE)) return false;
         if (!vldi(&C->accept)) continue;
 
         // ---- y_{k+1} = tau^p phi_p(tau A) w_p + sum_{j<p} tau^j/j! w_j (eq3.17)
@@ -681,15 +691,22 @@ __device__ __forceinline__ void phi_body(const PhiArgsT<R>& a) {
         }
         double v[1] = {(double)nzy};
         auto post_y = [](volatile PhiCtrl* c) { c->wnz[0] = c->red[0] > 0.0; };
-        if (!grid_reduce<1>(a, sh, v, PH_COMBINE, post_y)) goto finish;
+        if (!grid_reduce<1>(a, sh, v, PH_COMBINE, post_y)) return false;
         break;
       }
     }
   }
 
-finish:
-  // The last writer of the statistics is block 0 once everything has stopped.
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  return true;
+}
+
+// Statistics of one call, written by block 0 of the group once the call has
+// ended (normally or by abort).
+template <typename R>
+__device__ void phi_finish(const PhiArgsT<R>& a, Shared& sh) {
+  const int ng = a.T.ng;
+  PhiCtrl* C = a.ctrl;
+  if (sh.gb == 0 && threadIdx.x == 0) {
     DevStats* S = a.stats;
     int ab = ld_volatile_int(&a.sync->abort);
     int st = C->status != SWE_OK ? C->status : ab;
@@ -701,12 +718,119 @@ finish:
     if (S->status == SWE_OK) S->status = st;
     if (a.m_slot && st == SWE_OK && C->m_last > 0) *a.m_slot = C->m_last;
     if (a.prof) {
+      // per cell: IOM2 iteration 342 flop / 136 B, w_j product 310 / 104,
+      // combination term 8 / 32 (bytes of FP64 vectors; FP32 vectors move half)
+      const double cells = (double)ng, esz = (double)sizeof(R) / 8.0;
       a.prof->iters += C->n_iter;
       a.prof->wjv += C->n_wjv;
       a.prof->comb_terms += C->comb_terms;
       a.prof->launches += 1;
+      a.prof->flop += cells * (342.0 * C->n_iter + 310.0 * C->n_wjv + 8.0 * C->comb_terms);
+      a.prof->bytes += cells * esz * (136.0 * C->n_iter + 104.0 * C->n_wjv + 32.0 * C->comb_terms);
     }
   }
+}
+
+// ---------------------------------------------------------------------------
+// Ensemble launch: every member's group of blocks advances its exprb42
+// trajectory (stage passes, both phipm_simul_iom2 calls and the update) for
+// nsteps steps.  Members never wait on one another; each group has its own
+// barrier, control block and reduction buffer, so a member that stops (error)
+// does not hold the others.
+// ---------------------------------------------------------------------------
+constexpr int ENS_THREADS = 96;
+constexpr int ENS_MIN_BLOCKS = 4;
+
+__device__ bool ens_step(const EnsMember& M, Shared& sh) {
+  const Tables& T = M.c1.T;
+  const int ng = T.ng;
+  const int chunk = (ng + sh.gn - 1) / sh.gn;
+  const Range RG{min(ng, sh.gb * chunk), min(ng, (sh.gb + 1) * chunk)};
+  const CellLoop CL(RG);
+  double* S1 = M.tmpS;
+  double* S2 = M.tmpS + (size_t)4 * ng;
+  // eta, n x u of u_n and pass 1 of F(u_n)
+  FOR_CELLS(i) {
+    aux_cell(T, i, (const double*)M.u, M.aux);
+    pass1_cell<MODE_F>(T, i, (const double*)M.u, 1.0, (const double*)nullptr, S1, S2);
+  }
+  if (!grid_barrier(M.c1, sh, PH_PROLOGUE)) return false;
+  FOR_CELLS(i) {
+    double o[4];
+    pass2_cell<MODE_F>(T, i, (const double*)M.u, 1.0, S1, S2, (const double*)nullptr, o);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) M.vF[(size_t)c * ng + i] = M.dt * o[c];
+  }
+  if (!grid_barrier(M.c1, sh, PH_PROLOGUE)) return false;
+  // U_n2 - u_n = (3/4) dt phi_1((3/4) dt J) F(u_n)
+  bool ok = phi_run<double>(M.c1, sh);
+  phi_finish<double>(M.c1, sh);
+  if (!ok) return false;
+  // D_n2 = N(U_n2) - N(u_n) = Q(U_n2 - u_n); v_3 = (32/9) dt D_n2
+  FOR_CELLS(i) pass1_cell<MODE_Q>(T, i, (const double*)M.y1, 1.0, (const double*)nullptr, S1, S2);
+  if (!grid_barrier(M.c1, sh, PH_PROLOGUE)) return false;
+  const double c3 = (32.0 / 9.0) * M.dt;
+  FOR_CELLS(i) {
+    double o[4];
+    pass2_cell<MODE_Q>(T, i, (const double*)M.y1, 1.0, S1, S2, (const double*)nullptr, o);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) M.v3[(size_t)c * ng + i] = c3 * o[c];
+  }
+  if (!grid_barrier(M.c1, sh, PH_PROLOGUE)) return false;
+  // w = phi_1(A) v + phi_3(A) (32/9) dt D_n2; u_{n+1} = u_n + w
+  ok = phi_run<double>(M.c2, sh);
+  phi_finish<double>(M.c2, sh);
+  if (!ok) return false;
+  FOR_CELLS(i) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const size_t e = (size_t)c * ng + i;
+      M.u[e] = M.u[e] + M.w[e];
+    }
+  }
+  return grid_barrier(M.c1, sh, PH_PROLOGUE);
+}
+
+__global__ void __launch_bounds__(ENS_THREADS, ENS_MIN_BLOCKS)
+    ens_kernel(EnsMember* __restrict__ mem, const int* __restrict__ blk2mem) {
+  __shared__ Shared sh;
+  const int m = blk2mem[blockIdx.x];
+  EnsMember& M = mem[m];
+  if (threadIdx.x == 0) {
+    sh.gb = blockIdx.x - M.b0;
+    sh.gn = M.nb;
+    if (sh.gb == 0) M.t0 = globaltimer();
+  }
+  __syncthreads();
+  for (int s = 0; s < M.nsteps; ++s)
+    if (!ens_step(M, sh)) break;
+  if (threadIdx.x == 0 && sh.gb == 0) M.t1 = globaltimer();
+}
+
+int ens_max_blocks(int* nblocks, int* threads) {
+  int dev = 0, nsm = 0, per = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, ens_kernel, ENS_THREADS, 0) != cudaSuccess || per < 1)
+    return -1;
+  *nblocks = per * nsm;
+  *threads = ENS_THREADS;
+  return 0;
+}
+
+int launch_ens_kernel(EnsMember* mem, const int* blk2mem, int nblocks, cudaStream_t stream) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(nblocks);
+  cfg.blockDim = dim3(ENS_THREADS);
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  void* args[] = {(void*)&mem, (void*)&blk2mem};
+  cudaError_t e = cudaLaunchKernelExC(&cfg, (const void*)ens_kernel, args);
+  return e == cudaSuccess ? 0 : (int)e;
 }
 
 // Instantiations (block size, minimum resident blocks per SM for the register
@@ -714,7 +838,14 @@ finish:
 // least m_max + p + 1 = 69 threads.
 template <typename R, int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB) phi_kernel(const __grid_constant__ PhiArgsT<R> a) {
-  phi_body<R>(a);
+  __shared__ Shared sh;
+  if (threadIdx.x == 0) {
+    sh.gb = blockIdx.x;
+    sh.gn = gridDim.x;
+  }
+  __syncthreads();
+  phi_run<R>(a, sh);
+  phi_finish<R>(a, sh);
 }
 
 struct PhiVariant {

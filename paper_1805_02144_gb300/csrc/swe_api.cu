@@ -3,9 +3,12 @@
 // the exprb_step drivers of Sec. 4.4.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <memory>
+#include <numeric>
 #include <string>
 #include <vector>
 
@@ -18,6 +21,8 @@ namespace swe {
 template <class A>
 int launch_phi_kernel(const PhiLaunch& L, const A& a, cudaStream_t stream);
 int phi_select(int ng, int single, PhiLaunch* out);
+int ens_max_blocks(int* nblocks, int* threads);
+int launch_ens_kernel(EnsMember* mem, const int* blk2mem, int nblocks, cudaStream_t stream);
 }  // namespace swe
 
 using namespace swe;
@@ -86,6 +91,23 @@ struct swe_grid {
   size_t ev_used = 0;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> phi_ev, call_ev;
   int64_t kernel_launches = 0;
+};
+
+struct swe_ensemble {
+  int nmem = 0;
+  int nblocks = 0;            // blocks of the launch (all co-resident)
+  std::vector<swe_grid*> grids;
+  std::vector<EnsMember> hmem;
+  std::vector<int> nb;        // blocks per member
+  EnsMember* dmem = nullptr;
+  int* dblk = nullptr;        // block -> member
+  GridSync* dsync = nullptr;  // nmem
+  DevStats* dstats = nullptr; // nmem
+  void* dws = nullptr;        // member workspaces
+  double* backup = nullptr;   // states saved while tuning
+  std::vector<size_t> state_off;  // offset of member m's state in backup (doubles)
+  int* dslots = nullptr;      // 2 per member: Krylov size carried between steps and runs
+  int* dslots_backup = nullptr;
 };
 
 struct swe_scheme_state {
@@ -849,6 +871,286 @@ int exprb_step(swe_grid* g, int scheme, double dt, const double* u_n, double* u_
   return read_stats(g, stats, st);
 }
 
+// ---------------------------------------------------------------------------
+// ensembles
+// ---------------------------------------------------------------------------
+static int ens_upload_split(swe_ensemble* E) {
+  int b = 0;
+  std::vector<int> blk(E->nblocks, 0);
+  for (int m = 0; m < E->nmem; ++m) {
+    E->hmem[m].b0 = b;
+    E->hmem[m].nb = E->nb[m];
+    for (int k = 0; k < E->nb[m]; ++k) blk[b + k] = m;
+    b += E->nb[m];
+  }
+  if (b > E->nblocks) return fail(SWE_ERR_INVALID_ARG, "ensemble block split exceeds the launch");
+  E->nblocks = b;
+  CK(cudaMemcpy(E->dblk, blk.data(), (size_t)b * sizeof(int), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(E->dmem, E->hmem.data(), E->hmem.size() * sizeof(EnsMember), cudaMemcpyHostToDevice));
+  return SWE_OK;
+}
+
+// Blocks proportional to weights, at least one each, summing to total
+// (largest remainders).
+static std::vector<int> ens_split(const std::vector<double>& w, int total) {
+  const int n = (int)w.size();
+  double sum = 0.0;
+  for (double x : w) sum += x;
+  std::vector<int> nb(n, 1);
+  int left = total - n;
+  std::vector<std::pair<double, int>> rem;
+  int used = 0;
+  for (int m = 0; m < n; ++m) {
+    double share = sum > 0 ? left * w[m] / sum : 0.0;
+    int k = (int)share;
+    nb[m] += k;
+    used += k;
+    rem.push_back({share - k, m});
+  }
+  std::sort(rem.begin(), rem.end(), [](auto& a, auto& b) { return a.first > b.first; });
+  for (int r = 0; r < left - used && r < n; ++r) nb[rem[r].second] += 1;
+  return nb;
+}
+
+extern "C" int swe_ensemble_create(swe_grid* const* grids, int nmem, const double* dt, const int* nsteps,
+                                   const phi_opts* opts, swe_ensemble** out) {
+  if (!grids || !dt || !nsteps || !out || nmem < 1) return fail(SWE_ERR_INVALID_ARG, "ensemble: bad arguments");
+  *out = nullptr;
+  phi_opts o;
+  int rc = resolve_opts(opts, o);
+  if (rc) return rc;
+  if (o.precision != 0 || o.replay) return fail(SWE_ERR_INVALID_ARG, "ensemble: FP64 without replay only");
+  int NB = 0, threads = 0;
+  if (ens_max_blocks(&NB, &threads) != 0) return fail(SWE_ERR_CUDA, "ensemble: occupancy query failed");
+  if (nmem > NB) return fail(SWE_ERR_INVALID_ARG, "ensemble: more members than co-resident blocks");
+  for (int m = 0; m < nmem; ++m) {
+    if (!grids[m] || !grids[m]->dtab || !(dt[m] > 0.0) || nsteps[m] < 0)
+      return fail(SWE_ERR_INVALID_ARG, "ensemble: each member needs a device grid, dt > 0, nsteps >= 0");
+  }
+  std::unique_ptr<swe_ensemble> E(new swe_ensemble());
+  E->nmem = nmem;
+  E->nblocks = NB;
+  E->grids.assign(grids, grids + nmem);
+  // workspace layout per member (doubles): Vbuf (KMAX+1)n, W (PMAX+1)n, tmp 8ng, Lring 3n,
+  // Zbuf n, aux 4ng, part NB*NRED, u n, vF n, v3 n, y1 n, w n, tmpS 8ng  + ctrl, slots
+  auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+  std::vector<size_t> off(nmem);
+  size_t total = 0;
+  for (int m = 0; m < nmem; ++m) {
+    const size_t ng = grids[m]->T.ng, n = 4 * ng;
+    off[m] = total;
+    size_t d = (size_t)(KMAX + 1) * n + (size_t)(PMAX + 1) * n + 8 * ng + 3 * n + n + 4 * ng +
+               (size_t)NB * NRED + 5 * n + 8 * ng;
+    total += al(d * 8) + al(sizeof(PhiCtrl));
+  }
+  size_t nstates = 0;
+  for (int m = 0; m < nmem; ++m) {
+    E->state_off.push_back(nstates);
+    nstates += (size_t)4 * grids[m]->T.ng;
+  }
+  cudaError_t e = cudaMalloc(&E->dws, total);
+  if (e == cudaSuccess) e = cudaMalloc(&E->dmem, (size_t)nmem * sizeof(EnsMember));
+  if (e == cudaSuccess) e = cudaMalloc(&E->dblk, (size_t)NB * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&E->dsync, (size_t)nmem * sizeof(GridSync));
+  if (e == cudaSuccess) e = cudaMalloc(&E->dstats, (size_t)nmem * sizeof(DevStats));
+  if (e == cudaSuccess) e = cudaMalloc(&E->backup, nstates * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&E->dslots, (size_t)2 * nmem * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&E->dslots_backup, (size_t)2 * nmem * sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(E->dslots, 0, (size_t)2 * nmem * sizeof(int));
+  if (e != cudaSuccess) {
+    swe_ensemble_destroy(E.release());
+    return fail(SWE_ERR_NOMEM, std::string("ensemble allocation failed: ") + cudaGetErrorString(e));
+  }
+  if ((e = cudaMemset(E->dws, 0, total)) != cudaSuccess) {
+    swe_ensemble_destroy(E.release());
+    return cuda_fail(e, "cudaMemset(ensemble)");
+  }
+  E->hmem.resize(nmem);
+  std::vector<double> weight(nmem);
+  for (int m = 0; m < nmem; ++m) {
+    swe_grid* g = grids[m];
+    const size_t ng = g->T.ng, n = 4 * ng;
+    double* p = (double*)((char*)E->dws + off[m]);
+    auto take = [&](size_t cnt) {
+      double* q = p;
+      p += cnt;
+      return q;
+    };
+    EnsMember& M = E->hmem[m];
+    std::memset(&M, 0, sizeof(M));
+    double* Vbuf = take((size_t)(KMAX + 1) * n);
+    double* W = take((size_t)(PMAX + 1) * n);
+    double* tmp = take(8 * ng);
+    double* Lring = take(3 * n);
+    double* Zbuf = take(n);
+    double* aux = take(4 * ng);
+    double* part = take((size_t)NB * NRED);
+    M.u = take(n);
+    M.vF = take(n);
+    M.v3 = take(n);
+    M.y1 = take(n);
+    M.w = take(n);
+    M.tmpS = take(8 * ng);
+    M.aux = aux;
+    char* q = (char*)E->dws + off[m] + al(((size_t)(KMAX + 1) * n + (size_t)(PMAX + 1) * n + 8 * ng + 3 * n +
+                                             n + 4 * ng + (size_t)NB * NRED + 5 * n + 8 * ng) * 8);
+    PhiCtrl* ctrl = (PhiCtrl*)q;
+    int* slots = E->dslots + 2 * m;
+    M.dt = dt[m];
+    M.nsteps = nsteps[m];
+    for (int c = 0; c < 2; ++c) {
+      PhiArgs& a = c == 0 ? M.c1 : M.c2;
+      a.T = g->T;
+      a.u_lin = M.u;
+      a.aux = aux;
+      a.dt = dt[m];
+      a.ns = 1;
+      a.Vbuf = Vbuf;
+      a.W = W;
+      a.tmp = tmp;
+      a.Lring = Lring;
+      a.Zbuf = Zbuf;
+      a.part = part;
+      a.ctrl = ctrl;
+      a.sync = E->dsync + m;
+      a.stats = E->dstats + m;
+      a.prof = nullptr;
+      a.trace = nullptr;
+      a.trace_cap = 0;
+      a.call_index = c;
+      a.m_slot = o.m_carry ? slots + c : nullptr;
+      a.replay = nullptr;
+      a.n_replay = 0;
+      a.tol = o.tol;
+      a.delta = o.delta;
+      a.gamma = o.gamma;
+      a.kappa = o.kappa;
+      a.tol_mode = o.tol_mode;
+      a.m_init = o.m_init;
+      a.m_max = o.m_max;
+      a.max_reject = o.max_reject;
+      a.nA = g->host.nA;
+    }
+    M.c1.p = 1;
+    M.c1.rho[0] = 0.75;
+    M.c1.v[1] = M.vF;
+    M.c1.y_out[0] = M.y1;
+    M.c2.p = 3;
+    M.c2.rho[0] = 1.0;
+    M.c2.v[1] = M.vF;
+    M.c2.v[3] = M.v3;
+    M.c2.y_out[0] = M.w;
+    // work model: total Krylov iterations grow with dt * 2^level per step,
+    // i.e. with 2^level * (simulated time); cost per iteration with cells
+    weight[m] = (double)ng * std::pow(2.0, g->host.level) * dt[m] * (nsteps[m] > 0 ? nsteps[m] : 0) + 1.0;
+  }
+  E->nb = ens_split(weight, NB);
+  if ((rc = ens_upload_split(E.get()))) {
+    swe_ensemble_destroy(E.release());
+    return rc;
+  }
+  *out = E.release();
+  return SWE_OK;
+}
+
+extern "C" void swe_ensemble_destroy(swe_ensemble* E) {
+  if (!E) return;
+  if (E->dws) cudaFree(E->dws);
+  if (E->dmem) cudaFree(E->dmem);
+  if (E->dblk) cudaFree(E->dblk);
+  if (E->dsync) cudaFree(E->dsync);
+  if (E->dstats) cudaFree(E->dstats);
+  if (E->backup) cudaFree(E->backup);
+  if (E->dslots) cudaFree(E->dslots);
+  if (E->dslots_backup) cudaFree(E->dslots_backup);
+  delete E;
+}
+
+extern "C" int swe_ensemble_set_state(swe_ensemble* E, int m, const double* u, void* stream) {
+  if (!E || m < 0 || m >= E->nmem || !u) return fail(SWE_ERR_INVALID_ARG, "ensemble_set_state: bad arguments");
+  CK(cudaMemcpyAsync(E->hmem[m].u, u, (size_t)4 * E->grids[m]->T.ng * sizeof(double),
+                     cudaMemcpyDeviceToDevice, S(stream)));
+  return SWE_OK;
+}
+
+extern "C" int swe_ensemble_get_state(swe_ensemble* E, int m, double* u, void* stream) {
+  if (!E || m < 0 || m >= E->nmem || !u) return fail(SWE_ERR_INVALID_ARG, "ensemble_get_state: bad arguments");
+  CK(cudaMemcpyAsync(u, E->hmem[m].u, (size_t)4 * E->grids[m]->T.ng * sizeof(double),
+                     cudaMemcpyDeviceToDevice, S(stream)));
+  return SWE_OK;
+}
+
+extern "C" int swe_ensemble_reset(swe_ensemble* E, void* stream) {
+  if (!E) return fail(SWE_ERR_INVALID_ARG, "ensemble is NULL");
+  CK(cudaMemsetAsync(E->dslots, 0, (size_t)2 * E->nmem * sizeof(int), S(stream)));
+  return SWE_OK;
+}
+
+extern "C" int swe_ensemble_run(swe_ensemble* E, void* stream) {
+  if (!E) return fail(SWE_ERR_INVALID_ARG, "ensemble is NULL");
+  cudaStream_t st = S(stream);
+  CK(cudaMemsetAsync(E->dsync, 0, (size_t)E->nmem * sizeof(GridSync), st));
+  CK(cudaMemsetAsync(E->dstats, 0, (size_t)E->nmem * sizeof(DevStats), st));
+  int e = launch_ens_kernel(E->dmem, E->dblk, E->nblocks, st);
+  if (e != 0) return cuda_fail((cudaError_t)e, "cudaLaunchKernelEx(ens_kernel)");
+  return SWE_OK;
+}
+
+extern "C" int swe_ensemble_stats(swe_ensemble* E, phi_stats* stats, double* member_ms, int* member_blocks,
+                                  void* stream) {
+  if (!E) return fail(SWE_ERR_INVALID_ARG, "ensemble is NULL");
+  CK(cudaStreamSynchronize(S(stream)));
+  std::vector<DevStats> ds(E->nmem);
+  std::vector<EnsMember> hm(E->nmem);
+  CK(cudaMemcpy(ds.data(), E->dstats, ds.size() * sizeof(DevStats), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(hm.data(), E->dmem, hm.size() * sizeof(EnsMember), cudaMemcpyDeviceToHost));
+  for (int m = 0; m < E->nmem; ++m) {
+    if (stats) {
+      stats[m].n_jv = ds[m].n_jv;
+      stats[m].n_substeps = ds[m].n_sub;
+      stats[m].n_reject = ds[m].n_rej;
+      stats[m].m_last = ds[m].m_last;
+      stats[m].m_max_used = ds[m].m_max_used;
+      stats[m].status = ds[m].status;
+      stats[m].n_trace = 0;
+    }
+    if (member_ms) member_ms[m] = 1e-6 * (double)(hm[m].t1 - hm[m].t0);
+    if (member_blocks) member_blocks[m] = E->nb[m];
+  }
+  return SWE_OK;
+}
+
+extern "C" int swe_ensemble_tune(swe_ensemble* E, int rounds, void* stream) {
+  if (!E || rounds < 0) return fail(SWE_ERR_INVALID_ARG, "ensemble_tune: bad arguments");
+  cudaStream_t st = S(stream);
+  for (int m = 0; m < E->nmem; ++m)
+    CK(cudaMemcpyAsync(E->backup + E->state_off[m], E->hmem[m].u, (size_t)4 * E->grids[m]->T.ng * sizeof(double),
+                       cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(E->dslots_backup, E->dslots, (size_t)2 * E->nmem * sizeof(int), cudaMemcpyDeviceToDevice, st));
+  const int NB = std::accumulate(E->nb.begin(), E->nb.end(), 0);
+  for (int r = 0; r < rounds; ++r) {
+    int rc = swe_ensemble_run(E, stream);
+    if (rc) return rc;
+    std::vector<double> ms(E->nmem);
+    std::vector<phi_stats> ps(E->nmem);
+    if ((rc = swe_ensemble_stats(E, ps.data(), ms.data(), nullptr, stream))) return rc;
+    for (int m = 0; m < E->nmem; ++m)
+      if (ps[m].status != SWE_OK) return fail(ps[m].status, "ensemble_tune: a member failed");
+    // measured block-time of each member, then the split that equalises it
+    std::vector<double> w(E->nmem);
+    for (int m = 0; m < E->nmem; ++m) w[m] = ms[m] * E->nb[m];
+    E->nb = ens_split(w, NB);
+    E->nblocks = NB;
+    for (int m = 0; m < E->nmem; ++m)
+      CK(cudaMemcpyAsync(E->hmem[m].u, E->backup + E->state_off[m], (size_t)4 * E->grids[m]->T.ng * sizeof(double),
+                         cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(E->dslots, E->dslots_backup, (size_t)2 * E->nmem * sizeof(int), cudaMemcpyDeviceToDevice, st));
+    CK(cudaStreamSynchronize(st));
+    if ((rc = ens_upload_split(E))) return rc;
+  }
+  return SWE_OK;
+}
+
 int swe_profile_enable(swe_grid* g, int on) {
   if (!g) return fail(SWE_ERR_INVALID_ARG, "grid is NULL");
   int rc = ensure_workspace(g);
@@ -883,14 +1185,13 @@ int swe_profile_read(swe_grid* g, swe_profile* out, void* stream) {
     CK(cudaEventElapsedTime(&ms, pr.first, pr.second));
     out->call_ms += ms;
   }
-  const double ng = (double)g->T.ng;
   out->phi_launches = dp.launches;
   out->kernel_launches = g->kernel_launches;
   out->iom2_iterations = dp.iters;
   out->w_jv = dp.wjv;
   out->comb_terms = dp.comb_terms;
-  out->phi_flop = ng * (342.0 * dp.iters + 310.0 * dp.wjv + 8.0 * dp.comb_terms);
-  out->phi_bytes = ng * (136.0 * dp.iters + 104.0 * dp.wjv + 32.0 * dp.comb_terms);
+  out->phi_flop = dp.flop;
+  out->phi_bytes = dp.bytes;
   for (int k = 0; k < 10; ++k) out->phase_ms[k] = 1e-6 * (double)dp.phase_ns[k];
   return SWE_OK;
 }

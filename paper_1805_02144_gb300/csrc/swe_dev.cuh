@@ -34,17 +34,15 @@ using TablesF = TablesT<float>;
 enum StencilMode { MODE_F = 0, MODE_J = 1, MODE_Q = 2 };
 
 // ---------------------------------------------------------------------------
-// Loads.  Data produced inside the same persistent launch must not go through
-// the non-coherent read-only path, so kernels that write what they later
-// gather read with plain loads (`ld`); inputs fixed for the whole launch use
-// __ldg.  Operator tables are read once per cell and pass: they bypass L1
-// allocation and are marked first to leave L2, so that L1 and L2 keep the
-// gathered vectors (written one phase earlier).
+// Loads.  Vectors may be written inside the same persistent launch (basis,
+// stage vectors, and in an ensemble launch the states themselves), so they are
+// read with plain coherent loads (`ld`).  Operator tables are fixed for the
+// grid's life: they are read once per cell and pass through the non-coherent
+// path, bypass L1 allocation and are marked first to leave L2, so that L1 and
+// L2 keep the gathered vectors.
 // ---------------------------------------------------------------------------
 template <typename R>
 __device__ __forceinline__ R ld(const R* p) { return *p; }
-template <typename R>
-__device__ __forceinline__ R ldro(const R* p) { return __ldg(p); }
 
 __device__ __forceinline__ unsigned long long l2_evict_first_policy() {
   unsigned long long pol;
@@ -111,7 +109,7 @@ __device__ __forceinline__ void pass1_cell(const TablesT<R>& T, int i, const R* 
     for (int c = 0; c < 4; ++c) xv[c] *= sx;
     R uv[4];
 #pragma unroll
-    for (int c = 0; c < 4; ++c) uv[c] = ldro(u + (size_t)c * ng + i);
+    for (int c = 0; c < 4; ++c) uv[c] = ld(u + (size_t)c * ng + i);
     sq[i] = fma(uv[0], xv[0], fma(uv[1], xv[1], fma(uv[2], xv[2], T.g * xv[3])));
 #pragma unroll
     for (int c = 0; c < 3; ++c) sq[(size_t)(1 + c) * ng + i] = fma(xv[c], uv[3], uv[c] * xv[3]);
@@ -159,7 +157,7 @@ __device__ __forceinline__ R orth_pass1_cell(const TablesT<R>& T, int i, const R
   }
   R uv[4];
 #pragma unroll
-  for (int c = 0; c < 4; ++c) uv[c] = ldro(u + (size_t)c * ng + i);
+  for (int c = 0; c < 4; ++c) uv[c] = ld(u + (size_t)c * ng + i);
   sq[i] = fma(uv[0], zp[0], fma(uv[1], zp[1], fma(uv[2], zp[2], T.g * zp[3])));
 #pragma unroll
   for (int c = 0; c < 3; ++c) sq[(size_t)(1 + c) * ng + i] = fma(zp[c], uv[3], uv[c] * zp[3]);
@@ -255,14 +253,14 @@ __device__ __forceinline__ void aux_cell(const TablesT<R>& T, int i, const R* u,
   load_nbr(T, i, nb);
   R vor = R(0);
 #pragma unroll
-  for (int c = 0; c < 3; ++c) vor = fma(ldtab(T.vd + (size_t)c * ng + i), ldro(u + (size_t)c * ng + i), vor);
+  for (int c = 0; c < 3; ++c) vor = fma(ldtab(T.vd + (size_t)c * ng + i), ld(u + (size_t)c * ng + i), vor);
 #pragma unroll
   for (int k = 0; k < SLOTS; ++k)
 #pragma unroll
     for (int c = 0; c < 3; ++c)
-      vor = fma(ldtab(T.vc + ((size_t)c * SLOTS + k) * ng + i), ldro(u + (size_t)c * ng + nb[k]), vor);
+      vor = fma(ldtab(T.vc + ((size_t)c * SLOTS + k) * ng + i), ld(u + (size_t)c * ng + nb[k]), vor);
   R n0 = ldtab(T.nrm + i), n1 = ldtab(T.nrm + ng + i), n2 = ldtab(T.nrm + 2 * (size_t)ng + i);
-  R u0 = ldro(u + i), u1 = ldro(u + ng + i), u2 = ldro(u + 2 * (size_t)ng + i);
+  R u0 = ld(u + i), u1 = ld(u + ng + i), u2 = ld(u + 2 * (size_t)ng + i);
   aux[i] = fma(T.two_omega, n2, vor);
   aux[(size_t)ng + i] = n1 * u2 - n2 * u1;
   aux[2 * (size_t)ng + i] = n2 * u0 - n0 * u2;

@@ -98,3 +98,21 @@ def balanced_state(xyz: np.ndarray, seed: int, amplitude: float,
 def random_vector(n: int, seed: int) -> np.ndarray:
     """A seeded standard-normal vector (test directions, Krylov inputs)."""
     return np.random.Generator(np.random.PCG64(seed)).standard_normal(n)
+
+
+def ensemble_config(seed: int = 4, nmem: int = 64, levels=(5, 6, 7), dts=(900.0, 1800.0, 3600.0),
+                    horizon: float = 6 * 3600.0) -> list:
+    """Seeded ensemble members: level, dt, steps over the horizon, amplitude, seed.
+
+    Each member draws its grid level and time step uniformly from the given
+    sets and its perturbation amplitude from U[50, 400] m; nsteps = horizon/dt.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for m in range(nmem):
+        lev = int(rng.choice(levels))
+        dt = float(rng.choice(dts))
+        amp = float(rng.uniform(50.0, 400.0))
+        out.append({"level": lev, "dt": dt, "nsteps": int(round(horizon / dt)), "amplitude": amp,
+                    "seed": 1000 * seed + m})
+    return out
