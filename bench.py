@@ -21,6 +21,8 @@ import json
 import os
 import statistics
 import subprocess
+
+import numpy as np
 import sys
 import time
 
@@ -164,8 +166,138 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
+def timed_steps(G, u0, scheme, dt, nsteps, opts, flush, state=None, profile=False):
+    """nsteps steps from u0, one CUDA event pair per step on the current stream
+    (L2 flushed between steps outside the events).  Returns (per-step ms list,
+    final state, profile dict or None)."""
+    import torch
+    from paper_1805_02144_gb300.api import (SchemeState, exprb_step, swe_profile_enable,
+                                            swe_profile_read)
+    st = state if state is not None else SchemeState(G)
+    stream = torch.cuda.current_stream()
+    bufs = [u0.clone(), torch.empty_like(u0)]
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(nsteps)]
+    if profile:
+        swe_profile_enable(G, True)
+    torch.cuda.synchronize()
+    cur = 0
+    for k in range(nsteps):
+        flush.fill_(float(k))
+        ev[k][0].record(stream)
+        exprb_step(G, scheme, dt, bufs[cur], out=bufs[1 - cur], state=st, opts=opts)
+        ev[k][1].record(stream)
+        cur = 1 - cur
+    torch.cuda.synchronize()
+    prof = None
+    if profile:
+        prof = swe_profile_read(G)
+        swe_profile_enable(G, False)
+    return [a.elapsed_time(b) for a, b in ev], bufs[cur], prof
+
+
+def precision_block(flush) -> dict:
+    """Mixed precision vs FP64 on the level-8 exprb53 12 h run (same state)."""
+    import torch
+    from paper_1805_02144_gb300.api import Grid
+    from paper_1805_02144_gb300.inputs import balanced_state
+    G = Grid(8)
+    ng = G.ncells
+    u0 = torch.from_numpy(balanced_state(G.cell_centres(), 3, 400.0)).cuda()
+    res = {}
+    for name, opts in (("mixed", {"precision": 1, "tol": 1e-6}), ("fp64", {"tol": 1e-8})):
+        timed_steps(G, u0, "exprb53", 1800.0, 2, opts, flush)          # warm-up
+        ms, u, prof = timed_steps(G, u0, "exprb53", 1800.0, 24, opts, flush, profile=True)
+        tot = sum(ms)
+        res[name] = {"steps_per_s": 24 / (tot / 1e3), "ms_per_step": tot / 24, "tol": opts["tol"],
+                     "phi_share": prof["phi_ms"] / tot, "state": u}
+        if name == "mixed":
+            gbs = prof["phi_bytes"] / (prof["phi_ms"] / 1e3) / 1e9
+            hbm = _peaks().get("hbm_gbs", 6779.0)
+            res[name]["roofline"] = {"kernel": "phi_kernel<float>", "bound": "hbm", "achieved": gbs,
+                                     "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                                     "launch_ms": prof["phi_ms"] / max(prof["phi_launches"], 1)}
+    a, b = res["mixed"].pop("state").cpu().numpy(), res["fp64"].pop("state").cpu().numpy()
+    eh = float(np.linalg.norm(a[3 * ng:] - b[3 * ng:]) / np.linalg.norm(b[3 * ng:]))
+    ev = float(np.linalg.norm(a[:3 * ng] - b[:3 * ng]) / np.linalg.norm(b[:3 * ng]))
+    return {"workload": "exprb53, level-8 grid (655362 cells, n=2621448), dt=1800 s, 12 h "
+                        "(24 steps from the same seeded state, seed 3, 400 m)",
+            "mixed": res["mixed"], "fp64": res["fp64"],
+            "speedup_mixed_over_fp64": res["mixed"]["steps_per_s"] / res["fp64"]["steps_per_s"],
+            "rel_l2_mixed_vs_fp64": {"h": eh, "velocity": ev},
+            "note": "the FP64 path matches the FP64 oracle to 1e-10 (tests); mixed is within 1e-5"}
+
+
+def batching_block() -> dict:
+    """64-member exprb42 ensemble (levels 5/6/7, dt 900/1800/3600 s, 6 h) in one
+    persistent launch replayed from a CUDA graph, against the same trajectories
+    advanced one exprb_step at a time (the plain FP64 GPU form)."""
+    import torch
+    from paper_1805_02144_gb300.api import Ensemble, Grid, SchemeState, exprb_step
+    from paper_1805_02144_gb300.inputs import balanced_state, ensemble_config
+    cfg = ensemble_config()
+    grids = {lev: Grid(lev) for lev in sorted({c["level"] for c in cfg})}
+    gl = [grids[c["level"]] for c in cfg]
+    u0 = [torch.from_numpy(balanced_state(g.cell_centres(), c["seed"], c["amplitude"])).cuda()
+          for g, c in zip(gl, cfg)]
+    E = Ensemble(gl, [c["dt"] for c in cfg], [c["nsteps"] for c in cfg], opts={"tol": TOL})
+    for m, u in enumerate(u0):
+        E.set_state(m, u)
+    E.tune(rounds=2)
+
+    def reset():
+        for m, u in enumerate(u0):
+            E.set_state(m, u)
+        E.reset()
+
+    reset()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            E.run(stream=s)
+    torch.cuda.current_stream().wait_stream(s)
+    times = []
+    for rep in range(3):
+        reset()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        g.replay()
+        b.record()
+        torch.cuda.synchronize()
+        times.append(a.elapsed_time(b))
+    st = E.stats()
+    ens_ms = min(times)
+    member_steps = sum(c["nsteps"] for c in cfg)
+    # the same trajectories one exprb_step call at a time
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for m, (G, c) in enumerate(zip(gl, cfg)):
+        ss = SchemeState(G)
+        u = u0[m].clone()
+        out = torch.empty_like(u)
+        for _ in range(c["nsteps"]):
+            exprb_step(G, "exprb42", c["dt"], u, out=out, state=ss, opts={"tol": TOL})
+            u, out = out, u
+    b.record()
+    torch.cuda.synchronize()
+    seq_ms = a.elapsed_time(b)
+    mm = st["member_ms"]
+    return {"workload": "64 exprb42 members (seed 4): levels 5/6/7, dt 900/1800/3600 s, amplitudes "
+                        "U[50,400] m, 6 h each (804 member-steps), FP64, Tol 1e-8",
+            "ensemble_ms": ens_ms, "member_steps_per_s": member_steps / (ens_ms / 1e3),
+            "sequential_ms": seq_ms, "sequential_member_steps_per_s": member_steps / (seq_ms / 1e3),
+            "speedup_over_sequential": seq_ms / ens_ms,
+            "launch": "one cooperative launch per 6 h run, replayed from a CUDA graph",
+            "group_ms_max": max(mm), "group_ms_mean": sum(mm) / len(mm),
+            "blocks_per_member": {"min": min(st["blocks"]), "max": max(st["blocks"]),
+                                  "total": sum(st["blocks"])}}
+
+
 def gpu_arm(args) -> None:
-    import numpy as np
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -178,8 +310,7 @@ def gpu_arm(args) -> None:
 
     from paper_1805_02144_gb300 import build
     build.build()
-    from paper_1805_02144_gb300.api import (Grid, SchemeState, exprb_step, swe_profile_enable,
-                                            swe_profile_read)
+    from paper_1805_02144_gb300.api import Grid, SchemeState, exprb_step
     from paper_1805_02144_gb300.inputs import balanced_state
 
     G = Grid(LEVEL)
@@ -188,32 +319,16 @@ def gpu_arm(args) -> None:
     opts = {"tol": TOL}
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
-    bufs = [u0.clone(), torch.empty_like(u0)]
 
     sampler = ClockSampler(local)
-    for k in range(args.warmup):
-        exprb_step(G, SCHEME, DT, bufs[k % 2], out=bufs[(k + 1) % 2], state=st, opts=opts)
-    cur = args.warmup % 2
-    torch.cuda.synchronize()
+    _, uw, _ = timed_steps(G, u0, SCHEME, DT, args.warmup, opts, flush, state=st)
     if dist:
         dist.barrier()
-    swe_profile_enable(G, True)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
-    torch.cuda.synchronize()
-    for k in range(args.steps):
-        flush.fill_(float(k))
-        ev[k][0].record(stream)
-        exprb_step(G, SCHEME, DT, bufs[cur], out=bufs[1 - cur], state=st, opts=opts)
-        ev[k][1].record(stream)
-        cur = 1 - cur
-    torch.cuda.synchronize()
+    ms, ucur, prof = timed_steps(G, uw, SCHEME, DT, args.steps, opts, flush, state=st, profile=True)
     if dist:
         dist.barrier()
     clocks = sampler.stop()
-    prof = swe_profile_read(G)
-    swe_profile_enable(G, False)
-    t_ms = sum(a.elapsed_time(b) for a, b in ev)
+    t_ms = sum(ms)
     if dist:
         t = torch.tensor([t_ms], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -223,7 +338,7 @@ def gpu_arm(args) -> None:
     # end to end through the public API: pinned host state in, host state out
     n = G.n
     h_in = torch.empty(n, dtype=torch.float64, pin_memory=True)
-    h_in.copy_(bufs[cur].cpu())
+    h_in.copy_(ucur.cpu())
     h_out = torch.empty(n, dtype=torch.float64, pin_memory=True)
     d_in, d_out = torch.empty_like(u0), torch.empty_like(u0)
     ev2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -247,7 +362,7 @@ def gpu_arm(args) -> None:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e_ms = float(t.item())
     e2e = world * args.steps / (e_ms / 1e3)
-    finite = bool(torch.isfinite(bufs[cur]).all().item())
+    finite = bool(torch.isfinite(ucur).all().item())
 
     if rank != 0:
         if dist:
@@ -283,6 +398,9 @@ def gpu_arm(args) -> None:
         "clocks": clocks,
         "finite": finite,
     }
+    if world == 1 and not args.no_extra:
+        line["precision"] = precision_block(flush)
+        line["batching"] = batching_block()
     if world == 1 and not args.no_cpu_baseline:
         try:
             res = run_oracle_subprocess(1, 0)
@@ -306,6 +424,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the precision/batching blocks")
     args = ap.parse_args()
     if args.impl == "reference":
         reference_arm(args)
