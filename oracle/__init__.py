@@ -16,7 +16,11 @@ phi      phi-functions (eqs. (3.6)-(3.7)), the augmented-matrix exponential of
 phipm    phipm_simul_iom2 (Algorithm 1) with IOM2 and the substep controller
 schemes  EPI2 (eq. 3.5), exprb42 (eq. 3.11), pexprb43 (eq. 3.12),
          exprb53 (eq. 3.13) and epi3 (eq. 3.19), driven as in Sec. 4.4
+adjoint  gradient of EPI2 / exprb42 steps with the substep decisions frozen,
+         by torch.autograd of a torch float64 re-evaluation of the same map,
+         and the observation misfit of a forecast
 
-Everything is float64 numpy / scipy.sparse; library primitives used as steps
-are sparse matrix-vector products and ``scipy.linalg.expm``.
+Everything else is float64 numpy / scipy.sparse; library primitives used as
+steps are sparse matrix-vector products, ``scipy.linalg.expm``,
+``torch.linalg.matrix_exp`` and torch's reverse-mode differentiation.
 """

@@ -116,3 +116,42 @@ def ensemble_config(seed: int = 4, nmem: int = 64, levels=(5, 6, 7), dts=(900.0,
         out.append({"level": lev, "dt": dt, "nsteps": int(round(horizon / dt)), "amplitude": amp,
                     "seed": 1000 * seed + m})
     return out
+
+
+def observation_network(xyz: np.ndarray, nobs: int = 1000, seed: int = 7, sigma: float = 5.0,
+                        truth_seed: int = 8, truth_amplitude: float = 400.0):
+    """Synthetic height observations for the adjoint misfit.
+
+    Cells: the cell nearest to each of a seeded sequence of uniformly random
+    unit vectors, duplicates dropped, until ``nobs`` distinct cells are found
+    (so the set depends on positions only, not on the cell order).
+    Values: the height of a second balanced state (``truth_seed``) at those
+    cells plus Gaussian noise of standard deviation ``sigma`` [m].
+    Returns (cells, y, sigma) with cells indexing the caller's order.
+    """
+    ng = xyz.shape[0]
+    if not 0 < nobs <= ng:
+        raise ValueError("need 0 < nobs <= number of cells")
+    rng = np.random.Generator(np.random.PCG64(seed))
+    cells: list = []
+    seen = set()
+    while len(cells) < nobs:
+        d = rng.normal(size=(nobs, 3))
+        d /= np.linalg.norm(d, axis=1, keepdims=True)
+        for c in _nearest(xyz, d):
+            if int(c) not in seen:
+                seen.add(int(c))
+                cells.append(int(c))
+                if len(cells) == nobs:
+                    break
+    cells = np.asarray(cells, dtype=np.int64)
+    h_truth = H0 + height_perturbation(xyz[cells], truth_seed, truth_amplitude)[0]
+    noise = np.random.Generator(np.random.PCG64(seed + 1)).normal(size=nobs)
+    return cells, h_truth + sigma * noise, sigma
+
+
+def _nearest(xyz: np.ndarray, d: np.ndarray) -> np.ndarray:
+    out = np.empty(d.shape[0], dtype=np.int64)
+    for a in range(0, d.shape[0], 64):
+        out[a:a + 64] = np.argmax(d[a:a + 64] @ xyz.T, axis=1)
+    return out
