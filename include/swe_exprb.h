@@ -123,7 +123,11 @@ int swe_create_grid_host(int level, double radius, double g, double omega, doubl
  *   "vc", "vd" double: as nc, ndd with the edge tangent t_e
  * so that (L psi)_i = wld psi_i + sum_k wl psi_nbr, (D.q)_i = ndd.q_i +
  * sum_k nc.q_nbr, (V.u)_i = vd.u_i + sum_k vc.u_nbr and
- * (G psi)_i = P_i[(ndd - sdg) psi_i + sum_k nc psi_nbr]. */
+ * (G psi)_i = P_i[(ndd - sdg) psi_i + sum_k nc psi_nbr].
+ *   "wlT", "ncT", "vcT": the transposed slot tables, shaped as wl, nc, vc:
+ * slot k of cell j holds the coefficient that row i = nbr[k][j] of wl, nc, vc
+ * gives column j (0 in the pad slot of a pentagon), so that
+ * (L^T psi)_j = wld psi_j + sum_k wlT psi_nbr (the diagonals are shared). */
 int swe_grid_export(const swe_grid* grid, const char* table, void* host_out, int64_t count);
 
 /* Sizes and constants: ncells, n = 4*ncells, n_A = structural nonzeros of J
@@ -161,6 +165,21 @@ int swe_jv(const swe_grid* grid, const double* u, const double* x, double* jx, v
  * calls that overlap on the GPU (e.g. on two streams) race and must be
  * serialised by the caller.  u, x, jx: device, n doubles; jx distinct. */
 int swe_jv_noalloc(const swe_grid* grid, const double* u, const double* x, double* jx, void* stream);
+
+/* out = J(u)^T lam, the transpose of the Jacobian of Eqs. eq:dynja-eq:dynjc
+ * (the operator the adjoint of a step applies; the paper defines J, its
+ * transpose follows from it).  Each stencil row is transposed slot by slot
+ * with tables built on the host.  u, lam, out: device, n doubles; out must not
+ * overlap u or lam. */
+int swe_jtv(const swe_grid* grid, const double* u, const double* lam, double* out, void* stream);
+
+/* out = (J(x) - J(0))^T lam: the transpose of the derivative at x of the
+ * quadratic part Q of F (F(u) = J(0) u + Q(u), Sec. 2; J(x) = J(0) + Q'(x)).
+ * Because Q'(x) y is bilinear in (x, y), this is also the transpose, with
+ * respect to u, of d/du [J(u) y] at y = x: the term the adjoint of a Krylov
+ * projection with A = dt J(u_n) contributes to u_n.  x, lam, out: device,
+ * n doubles; out must not overlap x or lam. */
+int swe_dqtv(const swe_grid* grid, const double* x, const double* lam, double* out, void* stream);
 
 /* phipm_simul_iom2 (Sec. 4.3, Algorithm 1): for A = dt*J(u_lin) and vectors
  * v_0..v_p, writes y_out[i] = sum_{l=0}^{p} rho_i^l phi_l(rho_i A) v_l

@@ -70,7 +70,8 @@ class Grid:
         """Host copy of an operator table (see swe_grid_export), shaped [..., ncells]."""
         ng = self.ncells
         shapes = {"nbr": (6, ng), "wl": (6, ng), "wld": (ng,), "nc": (3, 6, ng), "ndd": (3, ng),
-                  "sdg": (3, ng), "vc": (3, 6, ng), "vd": (3, ng)}
+                  "sdg": (3, ng), "vc": (3, 6, ng), "vd": (3, ng), "wlT": (6, ng), "ncT": (3, 6, ng),
+                  "vcT": (3, 6, ng)}
         out = np.empty(shapes[table], dtype=np.int32 if table == "nbr" else np.float64)
         check(load().swe_grid_export(self.handle, table.encode(), out.ctypes.data_as(C.c_void_p),
                                      out.size))
@@ -108,6 +109,24 @@ def swe_jv(grid: Grid, u: torch.Tensor, x: torch.Tensor, out: Optional[torch.Ten
     out = _new(grid, u) if out is None else out
     check(load().swe_jv(grid.handle, _ptr(u, grid.n, "u"), _ptr(x, grid.n, "x"),
                         _ptr(out, grid.n, "out"), _stream(stream)))
+    return out
+
+
+def swe_jtv(grid: Grid, u: torch.Tensor, lam: torch.Tensor, out: Optional[torch.Tensor] = None,
+            stream=None) -> torch.Tensor:
+    """out = J(u)^T lam (transpose of the Jacobian of Eqs. (eq:dynja)-(eq:dynjc))."""
+    out = _new(grid, u) if out is None else out
+    check(load().swe_jtv(grid.handle, _ptr(u, grid.n, "u"), _ptr(lam, grid.n, "lam"),
+                         _ptr(out, grid.n, "out"), _stream(stream)))
+    return out
+
+
+def swe_dqtv(grid: Grid, x: torch.Tensor, lam: torch.Tensor, out: Optional[torch.Tensor] = None,
+             stream=None) -> torch.Tensor:
+    """out = (J(x) - J(0))^T lam (transposed derivative of the quadratic part of F at x)."""
+    out = _new(grid, x) if out is None else out
+    check(load().swe_dqtv(grid.handle, _ptr(x, grid.n, "x"), _ptr(lam, grid.n, "lam"),
+                          _ptr(out, grid.n, "out"), _stream(stream)))
     return out
 
 

@@ -347,6 +347,28 @@ int build_host_grid(int level, double radius, bool reorder, HostGrid& g, const c
       g.vd[(size_t)c * ng + ni] = vd[(size_t)c * ng + i];
     }
   }
+  // transposed slot tables
+  g.wlT.assign((size_t)kSlots * ng, 0.0);
+  g.ncT.assign((size_t)3 * kSlots * ng, 0.0);
+  g.vcT.assign((size_t)3 * kSlots * ng, 0.0);
+  for (int j = 0; j < ng; ++j) {
+    for (int k = 0; k < kSlots; ++k) {
+      const int i = g.nbr[(size_t)k * ng + j];
+      if (i == j) continue;  // pad slot of a pentagon
+      int s = -1;
+      for (int q = 0; q < kSlots; ++q)
+        if (g.nbr[(size_t)q * ng + i] == j) s = q;
+      if (s < 0) {
+        *err = "neighbour relation is not symmetric";
+        return -1;
+      }
+      g.wlT[(size_t)k * ng + j] = g.wl[(size_t)s * ng + i];
+      for (int c = 0; c < 3; ++c) {
+        g.ncT[((size_t)c * kSlots + k) * ng + j] = g.nc[((size_t)c * kSlots + s) * ng + i];
+        g.vcT[((size_t)c * kSlots + k) * ng + j] = g.vc[((size_t)c * kSlots + s) * ng + i];
+      }
+    }
+  }
   return 0;
 }
 

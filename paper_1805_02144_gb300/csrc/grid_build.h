@@ -25,6 +25,11 @@ struct HostGrid {
   std::vector<double> vc;           // [3][6][ng] edge-value weights x l_e t_e / A_i
   std::vector<double> vd;           // [3][ng]    self weight of the same
   int64_t nA = 0;                   // structural nonzeros of J
+  // transposed slot tables: cell j, slot k (neighbour i = nbr[k][j]) holds
+  // row i's coefficient for column j (diagonals are unchanged by transposition)
+  std::vector<double> wlT;          // [6][ng]
+  std::vector<double> ncT;          // [3][6][ng]
+  std::vector<double> vcT;          // [3][6][ng]
 };
 
 // Returns 0 on success; `err` receives a message otherwise.

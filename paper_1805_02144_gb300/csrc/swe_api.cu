@@ -149,6 +149,24 @@ __global__ void k_pass2(Tables T, const double* x, double sx, const double* tmp,
   }
 }
 
+template <int MODE>
+__global__ void k_pass1T(Tables T, const double* lam, const double* aux, double* t) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < T.ng; i += gridDim.x * blockDim.x)
+    pass1T_cell<MODE>(T, i, lam, aux, t);
+}
+
+template <int MODE>
+__global__ void k_pass2T(Tables T, const double* lam, const double* u, const double* aux, const double* t,
+                         double* out) {
+  const int ng = T.ng;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ng; i += gridDim.x * blockDim.x) {
+    double o[4];
+    pass2T_cell<MODE>(T, i, lam, u, aux, t, o);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) out[(size_t)c * ng + i] = o[c];
+  }
+}
+
 struct Comb {
   const double* x[6];
   double c[6];
@@ -264,7 +282,8 @@ int upload_grid(swe_grid* g) {
   };
   const int32_t* d_nbr = nullptr;
   const double *d_nrm = nullptr, *d_wl = nullptr, *d_wld = nullptr, *d_nc = nullptr, *d_ndd = nullptr,
-               *d_sdg = nullptr, *d_vc = nullptr, *d_vd = nullptr;
+               *d_sdg = nullptr, *d_vc = nullptr, *d_vd = nullptr, *d_wlT = nullptr, *d_ncT = nullptr,
+               *d_vcT = nullptr;
   // the kernels read the G diagonal ndd - sdg directly (table "sdg" of the
   // device copy holds that difference)
   std::vector<double> gdg(h.sdg.size());
@@ -274,7 +293,8 @@ int upload_grid(swe_grid* g) {
       {h.wl.data(), h.wl.size() * 8, (void**)&d_wl},     {h.wld.data(), h.wld.size() * 8, (void**)&d_wld},
       {h.nc.data(), h.nc.size() * 8, (void**)&d_nc},     {h.ndd.data(), h.ndd.size() * 8, (void**)&d_ndd},
       {gdg.data(), gdg.size() * 8, (void**)&d_sdg},  {h.vc.data(), h.vc.size() * 8, (void**)&d_vc},
-      {h.vd.data(), h.vd.size() * 8, (void**)&d_vd},
+      {h.vd.data(), h.vd.size() * 8, (void**)&d_vd},     {h.wlT.data(), h.wlT.size() * 8, (void**)&d_wlT},
+      {h.ncT.data(), h.ncT.size() * 8, (void**)&d_ncT},  {h.vcT.data(), h.vcT.size() * 8, (void**)&d_vcT},
   };
   size_t total = 0;
   for (auto& p : parts) total += (p.bytes + 255) & ~size_t(255);
@@ -298,6 +318,9 @@ int upload_grid(swe_grid* g) {
   T.gdg = d_sdg;
   T.vc = d_vc;
   T.vd = d_vd;
+  T.wlT = d_wlT;
+  T.ncT = d_ncT;
+  T.vcT = d_vcT;
   return SWE_OK;
 }
 
@@ -662,6 +685,9 @@ int swe_grid_export(const swe_grid* g, const char* table, void* out, int64_t cou
   if (t == "sdg") return put(h.sdg.data(), h.sdg.size(), 8);
   if (t == "vc") return put(h.vc.data(), h.vc.size(), 8);
   if (t == "vd") return put(h.vd.data(), h.vd.size(), 8);
+  if (t == "wlT") return put(h.wlT.data(), h.wlT.size(), 8);
+  if (t == "ncT") return put(h.ncT.data(), h.ncT.size(), 8);
+  if (t == "vcT") return put(h.vcT.data(), h.vcT.size(), 8);
   return fail(SWE_ERR_INVALID_ARG, std::string("unknown table ") + table);
 }
 
@@ -716,6 +742,41 @@ int swe_jv(const swe_grid* gc, const double* u, const double* x, double* jx, voi
   k_aux<double><<<nb, TPB, 0, st>>>(T, u, g->aux);
   k_pass1<MODE_J><<<nb, TPB, 0, st>>>(T, x, 1.0, u, g->tmp2);
   k_pass2<MODE_J><<<nb, TPB, 0, st>>>(T, x, 1.0, g->tmp2, g->aux, 1.0, jx);
+  CK(cudaGetLastError());
+  count_launches(g, 3);
+  return SWE_OK;
+}
+
+int swe_jtv(const swe_grid* gc, const double* u, const double* lam, double* out, void* stream) {
+  swe_grid* g = const_cast<swe_grid*>(gc);
+  if (!g || !u || !lam || !out) return fail(SWE_ERR_INVALID_ARG, "swe_jtv: NULL argument");
+  if (lam == out) return fail(SWE_ERR_INVALID_ARG, "swe_jtv: lam and out must not alias");
+  int rc = ensure_workspace(g);
+  if (rc) return rc;
+  const Tables& T = g->T;
+  cudaStream_t st = S(stream);
+  int nb = grid_blocks(T.ng);
+  k_aux<double><<<nb, TPB, 0, st>>>(T, u, g->aux);
+  k_pass1T<MODE_JT><<<nb, TPB, 0, st>>>(T, lam, g->aux, g->tmp2);
+  k_pass2T<MODE_JT><<<nb, TPB, 0, st>>>(T, lam, u, g->aux, g->tmp2, out);
+  CK(cudaGetLastError());
+  count_launches(g, 3);
+  return SWE_OK;
+}
+
+int swe_dqtv(const swe_grid* gc, const double* x, const double* lam, double* out, void* stream) {
+  swe_grid* g = const_cast<swe_grid*>(gc);
+  if (!g || !x || !lam || !out) return fail(SWE_ERR_INVALID_ARG, "swe_dqtv: NULL argument");
+  if (lam == out) return fail(SWE_ERR_INVALID_ARG, "swe_dqtv: lam and out must not alias");
+  int rc = ensure_workspace(g);
+  if (rc) return rc;
+  Tables T0 = g->T;
+  T0.two_omega = 0.0;  // eta of x without the planetary vorticity
+  cudaStream_t st = S(stream);
+  int nb = grid_blocks(T0.ng);
+  k_aux<double><<<nb, TPB, 0, st>>>(T0, x, g->aux);
+  k_pass1T<MODE_QT><<<nb, TPB, 0, st>>>(T0, lam, g->aux, g->tmp2);
+  k_pass2T<MODE_QT><<<nb, TPB, 0, st>>>(T0, lam, x, g->aux, g->tmp2, out);
   CK(cudaGetLastError());
   count_launches(g, 3);
   return SWE_OK;

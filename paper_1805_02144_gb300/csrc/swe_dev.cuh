@@ -26,6 +26,10 @@ struct TablesT {
   const R* __restrict__ gdg;   // [3][ng] G diagonal (ndd - sdg of the host tables)
   const R* __restrict__ vc;    // [3][6][ng]
   const R* __restrict__ vd;    // [3][ng]
+  // transposed slot tables (FP64 grids only; see grid_build.h)
+  const R* __restrict__ wlT;   // [6][ng]
+  const R* __restrict__ ncT;   // [3][6][ng]
+  const R* __restrict__ vcT;   // [3][6][ng]
 };
 using Tables = TablesT<double>;
 using TablesF = TablesT<float>;
@@ -265,6 +269,105 @@ __device__ __forceinline__ void aux_cell(const TablesT<R>& T, int i, const R* u,
   aux[(size_t)ng + i] = n1 * u2 - n2 * u1;
   aux[2 * (size_t)ng + i] = n2 * u0 - n0 * u2;
   aux[3 * (size_t)ng + i] = n0 * u1 - n1 * u0;
+}
+
+// ---------------------------------------------------------------------------
+// Transposed stencils (adjoint).  With J x = -(V x_u) P - eta (n x x_u)
+// - G s(x) - nu L L x, continuity -D q(x) - nu L L x_h, where
+// s(x) = u.x_u + g x_h, q(x) = x_u h + u x_h, P = n x u, eta = V u + f and
+// G = P_n R (P_n = I - n n^T the tangent projection), the transpose is
+//   xbar_u,d = -(V_d^T a) + eta (n x lam_u) + u sbar + h qbar
+//   xbar_h   = g sbar + u.qbar
+//   xbar    += -nu L^T L^T lam                          (each variable)
+// with a = P.lam_u, sbar = -sum_c R_c^T (P_n lam_u)_c, qbar_c = -D_c^T lam_h.
+// MODE_JT: J(u)^T lam (aux = eta, P of u).
+// MODE_QT: (J(x) - J(0))^T lam, the transposed derivative of the quadratic
+// part at x: eta = V x without f, no g term, no dissipation (aux of x with
+// two_omega = 0).
+// ---------------------------------------------------------------------------
+enum TransMode { MODE_JT = 0, MODE_QT = 1 };
+
+// Pass 1 at cell i: t planes [a, (P_n lam_u) x 3, L^T lam x 4 (MODE_JT)].
+template <int MODE>
+__device__ __forceinline__ void pass1T_cell(const Tables& T, int i, const double* lam, const double* aux,
+                                            double* t) {
+  const int ng = T.ng;
+  double lu[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) lu[c] = ld(lam + (size_t)c * ng + i);
+  double p0 = ld(aux + (size_t)ng + i), p1 = ld(aux + 2 * (size_t)ng + i), p2 = ld(aux + 3 * (size_t)ng + i);
+  t[i] = fma(p0, lu[0], fma(p1, lu[1], p2 * lu[2]));
+  double n0 = ldtab(T.nrm + i), n1 = ldtab(T.nrm + ng + i), n2 = ldtab(T.nrm + 2 * (size_t)ng + i);
+  double nl = fma(n0, lu[0], fma(n1, lu[1], n2 * lu[2]));
+  t[(size_t)ng + i] = fma(-n0, nl, lu[0]);
+  t[2 * (size_t)ng + i] = fma(-n1, nl, lu[1]);
+  t[3 * (size_t)ng + i] = fma(-n2, nl, lu[2]);
+  if (MODE == MODE_JT) {
+    int nb[SLOTS];
+    load_nbr(T, i, nb);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const double* psi = lam + (size_t)c * ng;
+      double acc = ldtab(T.wld + i) * ld(psi + i);
+#pragma unroll
+      for (int k = 0; k < SLOTS; ++k) acc = fma(ldtab(T.wlT + (size_t)k * ng + i), ld(psi + nb[k]), acc);
+      t[(size_t)(4 + c) * ng + i] = acc;
+    }
+  }
+}
+
+// Pass 2 at cell j: out[4] = (J^T lam)_j (MODE_JT) or ((J(x)-J(0))^T lam)_j
+// (MODE_QT).  u: linearisation state (x for MODE_QT); aux: its eta, P.
+template <int MODE>
+__device__ __forceinline__ void pass2T_cell(const Tables& T, int j, const double* lam, const double* u,
+                                            const double* aux, const double* t, double out[4]) {
+  const int ng = T.ng;
+  int nb[SLOTS];
+  load_nbr(T, j, nb);
+  double va[3], sb = 0.0, qb[3];
+  const double aj = ld(t + j), lhj = ld(lam + 3 * (size_t)ng + j);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    va[c] = ldtab(T.vd + (size_t)c * ng + j) * aj;
+    sb = fma(ldtab(T.gdg + (size_t)c * ng + j), ld(t + (size_t)(1 + c) * ng + j), sb);
+    qb[c] = ldtab(T.ndd + (size_t)c * ng + j) * lhj;
+  }
+#pragma unroll
+  for (int k = 0; k < SLOTS; ++k) {
+    const int i = nb[k];
+    const double ai = ld(t + i), lhi = ld(lam + 3 * (size_t)ng + i);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const double w = ldtab(T.ncT + ((size_t)c * SLOTS + k) * ng + j);
+      va[c] = fma(ldtab(T.vcT + ((size_t)c * SLOTS + k) * ng + j), ai, va[c]);
+      sb = fma(w, ld(t + (size_t)(1 + c) * ng + i), sb);
+      qb[c] = fma(w, lhi, qb[c]);
+    }
+  }
+  sb = -sb;
+  double n0 = ldtab(T.nrm + j), n1 = ldtab(T.nrm + ng + j), n2 = ldtab(T.nrm + 2 * (size_t)ng + j);
+  double l0 = ld(lam + j), l1 = ld(lam + (size_t)ng + j), l2 = ld(lam + 2 * (size_t)ng + j);
+  double eta = ld(aux + j);
+  double uv[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) uv[c] = ld(u + (size_t)c * ng + j);
+  // eta (n x lam_u)
+  double r0 = eta * (n1 * l2 - n2 * l1), r1 = eta * (n2 * l0 - n0 * l2), r2 = eta * (n0 * l1 - n1 * l0);
+  out[0] = fma(uv[0], sb, fma(-uv[3], qb[0], r0 - va[0]));
+  out[1] = fma(uv[1], sb, fma(-uv[3], qb[1], r1 - va[1]));
+  out[2] = fma(uv[2], sb, fma(-uv[3], qb[2], r2 - va[2]));
+  out[3] = -fma(uv[0], qb[0], fma(uv[1], qb[1], uv[2] * qb[2]));
+  if (MODE == MODE_JT) {
+    out[3] = fma(T.g, sb, out[3]);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const double* psi = t + (size_t)(4 + c) * ng;
+      double acc = ldtab(T.wld + j) * ld(psi + j);
+#pragma unroll
+      for (int k = 0; k < SLOTS; ++k) acc = fma(ldtab(T.wlT + (size_t)k * ng + j), ld(psi + nb[k]), acc);
+      out[c] = fma(-T.nu, acc, out[c]);
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------

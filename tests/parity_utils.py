@@ -96,3 +96,35 @@ def stencil_tol(s) -> float:
     operator coefficients that differ by that much; 20x margin, floor 1e-13.
     """
     return max(1e-13, 20 * 1.1e-16 * s.ng / (4 * np.pi))
+
+
+def abs_jacobian(s, u: np.ndarray, quad_only: bool = False):
+    """Sparse matrix of the summed |terms| of J(u) (or of J(u) - J(0)).
+
+    Entry (r, c) bounds the sum of absolute values of every product that the
+    stencil adds into J_rc, so |J|^T |lam| bounds the terms of (J^T lam)_c.
+    """
+    import scipy.sparse as sp
+    ops = s.ops
+    A = abs
+    ux, uy, uz, h = s.split(u)
+    au = [np.abs(ux), np.abs(uy), np.abs(uz)]
+    P = [np.abs(c) for c in s.cross_n(ux, uy, uz)]
+    eta = sum(A(ops.V[d]) @ au[d] for d in range(3)) + (0.0 if quad_only else np.abs(s.f))
+    L = A(ops.L)
+    dis = None if quad_only else s.nu * (L @ L)
+    dg = sp.diags
+    blocks = [[None] * 4 for _ in range(4)]
+    for c in range(3):
+        for d in range(3):
+            t = dg(P[c]) @ A(ops.V[d]) + A(ops.G[c]) @ dg(au[d])
+            if c != d:
+                t = t + dg(eta)
+            elif dis is not None:
+                t = t + dis
+            blocks[c][d] = t
+        blocks[c][3] = None if quad_only else s.g * A(ops.G[c])
+        blocks[3][c] = A(ops.D[c]) @ dg(np.abs(h))
+    hh = sum(A(ops.D[d]) @ dg(au[d]) for d in range(3))
+    blocks[3][3] = hh if dis is None else hh + dis
+    return sp.bmat(blocks, format="csr")

@@ -92,6 +92,29 @@ def test_library_grid_equals_oracle_grid(lib, lev):
         close(to_oracle(raw[c] - sp.diags(nrm[:, c]) @ nR), ops.G[c])
 
 
+@pytest.mark.parametrize("lev", [0, 2, 4])
+def test_transposed_slot_tables(lib, lev):
+    """The transposed tables (used by J^T) give exactly the transposed matrices."""
+    from paper_1805_02144_gb300.api import Grid
+    G = Grid(lev, host_only=True)
+    ng = G.ncells
+    nbr = G.export("nbr")
+    wld, ndd, vd = G.export("wld"), G.export("ndd"), G.export("vd")
+
+    def same(A, B):
+        assert abs(A - B).max() == 0.0
+
+    same(_slot_matrix(nbr, G.export("wlT"), wld, ng), _slot_matrix(nbr, G.export("wl"), wld, ng).T)
+    nc, ncT, vc, vcT = G.export("nc"), G.export("ncT"), G.export("vc"), G.export("vcT")
+    for c in range(3):
+        same(_slot_matrix(nbr, ncT[c], ndd[c], ng), _slot_matrix(nbr, nc[c], ndd[c], ng).T)
+        same(_slot_matrix(nbr, vcT[c], vd[c], ng), _slot_matrix(nbr, vc[c], vd[c], ng).T)
+    # the pad slot of each pentagon carries no weight in either table
+    pad = nbr == np.arange(ng)[None, :]
+    assert pad.sum() == 12
+    assert not np.any(G.export("wl")[pad]) and not np.any(G.export("wlT")[pad])
+
+
 def test_hilbert_order_improves_locality(lib):
     from paper_1805_02144_gb300.api import Grid
     spread = {}
