@@ -63,7 +63,8 @@ typedef struct {
   int m_carry;       /* exprb_step: start each call slot at its last accepted m    */
   const double* replay;  /* host, optional: 3 doubles (tau, m, accepted) per attempt;
                             when non-NULL the step sizes, Krylov sizes and decisions
-                            are taken from it instead of the controller            */
+                            are taken from it instead of the controller (exprb_step:
+                            the records of all the step's phi calls, in call order) */
   int n_replay;      /* number of attempts in replay                               */
   int precision;     /* 0: FP64 throughout.  1: mixed -- stencils, Krylov basis and
                         stage vectors of the phi evaluations in FP32 (FP32 operator
@@ -209,6 +210,31 @@ void swe_scheme_state_destroy(swe_scheme_state* st);
  * the step's phi calls. */
 int exprb_step(swe_grid* grid, int scheme, double dt, const double* u_n, double* u_np1,
                swe_scheme_state* state, const phi_opts* opts, phi_stats* stats, void* stream);
+
+/* Adjoint of one exprb_step: lam_n = (d u_{n+1} / d u_n)^T lam_np1 with the
+ * substep decisions of the forward step frozen (the paper defines no
+ * adjoint; the derivative is the one of the computed step, Algorithm 1 with
+ * the step sizes, Krylov sizes and accept/reject choices of `trace`).
+ *   scheme: SWE_EPI2 or SWE_EXPRB42 (Eqs. eq3.5, eq3.11).
+ *   u_n: the step's input state (device, n doubles), the checkpoint.
+ *   trace: host array of the forward step's n_trace attempts, as exprb_step
+ *     wrote them into phi_stats.trace (call indices 0..ncalls-1 in order).
+ *   lam_np1: device, n doubles, adjoint of u_{n+1}; lam_n: device output,
+ *     must not alias lam_np1 or u_n.
+ *   opts: NULL or FP64 options (precision must be 0); the replay fields are
+ *     ignored (the trace is the replay).
+ * The step is recomputed from u_n in replay mode with every accepted
+ * substep's w_j, Krylov basis and small matrices kept on a device tape
+ * (grown as needed and owned by the grid), then one persistent launch per
+ * phipm_simul_iom2 call runs the reverse sweep, with J(u_n)^T and the
+ * transposed derivative of J(u_n) x with respect to u_n applied by
+ * transposed stencils.  stats (optional) reports the recomputation's counts
+ * and status.  Waits for the stream.  A trace that does not match the
+ * scheme, or a Krylov breakdown in a recorded substep, gives
+ * SWE_ERR_INVALID_ARG. */
+int exprb_step_adjoint(swe_grid* grid, int scheme, double dt, const double* u_n, const phi_attempt* trace,
+                       int n_trace, const double* lam_np1, double* lam_n, const phi_opts* opts,
+                       phi_stats* stats, void* stream);
 
 /* Opt-in timing and operation counts (CUDA events recorded on the call's
  * stream around every persistent phi launch and every exprb_step / phi_action

@@ -24,7 +24,7 @@ EXPORTS = ["swe_phi_opts_default", "swe_create_grid", "swe_create_grid_host", "s
            "swe_grid_cell_centres", "swe_grid_cell_areas", "swe_rhs", "swe_jv", "swe_jv_noalloc",
            "swe_jtv", "swe_dqtv", "phi_action",
            "swe_scheme_state_create", "swe_scheme_state_reset", "swe_scheme_state_destroy",
-           "exprb_step", "swe_profile_enable", "swe_profile_read", "swe_device_status",
+           "exprb_step", "exprb_step_adjoint", "swe_profile_enable", "swe_profile_read", "swe_device_status",
            "swe_last_error", "swe_ensemble_create", "swe_ensemble_destroy", "swe_ensemble_set_state",
            "swe_ensemble_get_state", "swe_ensemble_run", "swe_ensemble_reset", "swe_ensemble_tune",
            "swe_ensemble_stats"]
@@ -103,6 +103,8 @@ def load(path: Optional[str] = None) -> C.CDLL:
     L.swe_scheme_state_destroy.restype = None
     L.exprb_step.argtypes = [vp, C.c_int, C.c_double, vp, vp, vp, C.POINTER(PhiOptsC),
                              C.POINTER(PhiStatsC), vp]
+    L.exprb_step_adjoint.argtypes = [vp, C.c_int, C.c_double, vp, C.POINTER(PhiAttemptC), C.c_int, vp, vp,
+                                     C.POINTER(PhiOptsC), C.POINTER(PhiStatsC), vp]
     L.swe_profile_enable.argtypes = [vp, C.c_int]
     L.swe_profile_read.argtypes = [vp, C.POINTER(ProfileC), vp]
     L.swe_device_status.argtypes = [vp, vp]
@@ -121,7 +123,7 @@ def load(path: Optional[str] = None) -> C.CDLL:
     for name in ("swe_create_grid", "swe_create_grid_host", "swe_grid_export", "swe_grid_query", "swe_grid_cell_centres", "swe_grid_cell_areas",
                  "swe_rhs", "swe_jv", "swe_jv_noalloc", "swe_jtv", "swe_dqtv", "phi_action",
                  "swe_scheme_state_create",
-                 "swe_scheme_state_reset", "exprb_step", "swe_device_status", "swe_profile_enable",
+                 "swe_scheme_state_reset", "exprb_step", "exprb_step_adjoint", "swe_device_status", "swe_profile_enable",
                  "swe_profile_read", "swe_ensemble_create", "swe_ensemble_set_state",
                  "swe_ensemble_get_state", "swe_ensemble_run", "swe_ensemble_reset", "swe_ensemble_tune",
                  "swe_ensemble_stats"):

@@ -222,6 +222,67 @@ def exprb_step(grid: Grid, scheme: str, dt: float, u_n: torch.Tensor,
     return (out, _stats_dict(st)) if st is not None else out
 
 
+def _trace_array(trace) -> tuple:
+    """phi_attempt array from exprb_step's stats["trace"] (list of dicts)."""
+    arr = (PhiAttemptC * len(trace))()
+    for i, r in enumerate(trace):
+        arr[i].t = float(r["t"])
+        arr[i].tau = float(r["tau"])
+        arr[i].omega = float(r.get("omega", 0.0))
+        arr[i].m = int(r["m"])
+        arr[i].accepted = int(bool(r["accepted"]))
+        arr[i].call = int(r["call"])
+    return arr
+
+
+def exprb_step_adjoint(grid: Grid, scheme: str, dt: float, u_n: torch.Tensor, trace, lam_np1: torch.Tensor,
+                       out: Optional[torch.Tensor] = None, opts=None, stats: bool = False, stream=None):
+    """lam_n = (d u_{n+1}/d u_n)^T lam_np1 with the decisions of ``trace`` frozen
+    (``trace``: exprb_step's stats["trace"] for the step from u_n)."""
+    if not trace:
+        raise ValueError("exprb_step_adjoint needs the forward step's trace")
+    out = _new(grid, u_n) if out is None else out
+    o, keep = _opts(opts)
+    arr = _trace_array(trace)
+    st = PhiStatsC() if stats else None
+    check(load().exprb_step_adjoint(grid.handle, SCHEMES[scheme], float(dt), _ptr(u_n, grid.n, "u_n"), arr,
+                                    len(trace), _ptr(lam_np1, grid.n, "lam_np1"), _ptr(out, grid.n, "out"),
+                                    C.byref(o), C.byref(st) if st is not None else None, _stream(stream)))
+    del keep
+    return (out, _stats_dict(st)) if st is not None else out
+
+
+class ExprbStepFunction(torch.autograd.Function):
+    """u_{n+1} = exprb_step(u_n) with backward = exprb_step_adjoint (frozen decisions).
+
+    The input u_n is the checkpoint; backward recomputes the step from it."""
+
+    @staticmethod
+    def forward(ctx, u_n, grid, scheme, dt, state, opts, trace_cap):
+        out, st = exprb_step(grid, scheme, dt, u_n.detach(), state=state, opts=opts, stats=True,
+                             trace_cap=trace_cap)
+        if st["status"] != 0:
+            raise RuntimeError(f"exprb_step failed on the device: status {st['status']}")
+        if len(st["trace"]) >= trace_cap:
+            raise RuntimeError("trace_cap too small for the step's attempts")
+        ctx.save_for_backward(u_n.detach())
+        ctx.meta = (grid, scheme, dt, st["trace"], opts)
+        return out
+
+    @staticmethod
+    def backward(ctx, g):
+        (u_n,) = ctx.saved_tensors
+        grid, scheme, dt, trace, opts = ctx.meta
+        lam = exprb_step_adjoint(grid, scheme, dt, u_n, trace, g.contiguous(), opts=opts)
+        return lam, None, None, None, None, None, None
+
+
+def exprb_step_differentiable(grid: Grid, scheme: str, dt: float, u_n: torch.Tensor, state: "SchemeState",
+                              opts=None, trace_cap: int = 4096) -> torch.Tensor:
+    """exprb_step as a torch autograd node (EPI2 and exprb42)."""
+    return ExprbStepFunction.apply(u_n, grid, scheme, dt, state, opts, trace_cap)
+
+
 def swe_device_status(grid: Grid, stream=None) -> None:
     check(load().swe_device_status(grid.handle, _stream(stream)))
 

@@ -17,7 +17,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libswe_exprb.so")
-SOURCES = ["grid_build.cpp", "swe_api.cu", "phi_kernel.cu", "swe_noalloc.cu"]
+SOURCES = ["grid_build.cpp", "swe_api.cu", "phi_kernel.cu", "adj_kernel.cu", "swe_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O3",
          "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]

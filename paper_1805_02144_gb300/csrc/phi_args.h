@@ -47,6 +47,17 @@ struct PhiCtrl {
   int n_iter, n_wjv, comb_terms, pad;
 };
 
+// Scalars of one accepted substep kept for the adjoint (tape mode).
+struct TapeSub {
+  double t, tau, beta, hnext;
+  int m, s, land, out_idx;  // s: scaling steps of the exponential
+  int broken, pad0;
+  int wnz[PMAX + 1];        // w_j != 0 (zero skip of Eq. eq3.18)
+  int pad1;
+  double sig[KMAX + 2];     // basis vector j = sig[j] * raw slot j
+  double hd[KMAX + 1], hu[KMAX + 1], hl[KMAX + 2];
+};
+
 // The persistent-kernel instantiation chosen for a grid.
 struct PhiLaunch {
   const void* fn = nullptr;
@@ -84,6 +95,14 @@ struct PhiArgsT {
   int* m_slot;              // nullable: initial m (if > 0), receives m_last
   const double* replay;     // nullable device array, 3 doubles per attempt
   int n_replay;
+  // tape (adjoint recording, nullptr = off).  Accepted substep k keeps w_j in
+  // tapeW + k (p+1) n + j n and raw basis slot j >= 1 in tapeV + tape_offV[k]
+  // + j n; y_{k+1} is written to slot 0 of region k + 1.
+  R* tapeW;
+  R* tapeV;
+  const long long* tape_offV;
+  TapeSub* tape_sub;
+  int tape_cap;             // accepted substeps the tape holds
   // options
   double tol, delta, gamma, kappa;
   int tol_mode, m_init, m_max, max_reject;

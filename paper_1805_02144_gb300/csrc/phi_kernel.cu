@@ -20,6 +20,7 @@
 #include <cmath>
 
 #include "../../include/swe_exprb.h"
+#include "grid_ops.cuh"
 #include "phi_args.h"
 #include "swe_dev.cuh"
 
@@ -27,48 +28,6 @@ namespace swe {
 
 constexpr int PHI_MAX_THREADS = 256;  // largest block size of any instantiation
 constexpr double TAYLOR_THETA = 4.0;
-
-__device__ __forceinline__ double vld(const double* p) { return *(volatile const double*)p; }
-__device__ __forceinline__ int vldi(const int* p) { return *(volatile const int*)p; }
-
-struct Range {
-  int c0, c1;
-};
-
-// Cells of this thread inside the block's range (block-strided).
-struct CellLoop {
-  int first, end, step;
-  __device__ CellLoop(const Range& R) {
-    first = R.c0 + threadIdx.x;
-    end = R.c1;
-    step = blockDim.x;
-  }
-};
-#define FOR_CELLS(i) for (int i = CL.first; i < CL.end; i += CL.step)
-
-// ---------------------------------------------------------------------------
-// block reductions in a fixed order
-// ---------------------------------------------------------------------------
-template <int K>
-__device__ __forceinline__ void block_sum(double (&v)[K], double* sred) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int k = 0; k < K; ++k)
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
-  if (lane == 0)
-#pragma unroll
-    for (int k = 0; k < K; ++k) sred[warp * NRED + k] = v[k];
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int k = 0; k < K; ++k) {
-      double s = 0.0;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sred[w * NRED + k];
-      v[k] = s;
-    }
-  }
-  __syncthreads();
-}
 
 // Phase classes timed by block 0 while profiling: time from the end of the
 // previous barrier to the end of this one (work plus wait).
@@ -91,82 +50,39 @@ struct Shared {
   double scal[4];
 };
 
-template <class A>
-__device__ __forceinline__ void phase_tick(const A& a, Shared& sh, int phase) {
-  if (a.prof && sh.gb == 0 && threadIdx.x == 0) {
-    unsigned long long now = globaltimer();
-    a.prof->phase_ns[phase] += (long long)(now - sh.t_last);
-    sh.t_last = now;
-  }
-}
 
-// Plain grid barrier.  Returns false (uniformly per block) when the launch is
-// being aborted.
-template <class A>
-__device__ bool grid_barrier(const A& a, Shared& sh, int phase) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    bool last;
-    unsigned int gen = bar_arrive(a.sync, sh.gn, &last);
-    bool ok = true;
-    if (last)
-      bar_release(a.sync, gen);
-    else
-      ok = bar_wait(a.sync, gen, SWE_ERR_TIMEOUT);
-    sh.ok = ok && (ld_volatile_int(&a.sync->abort) == 0);
-    phase_tick(a, sh, phase);
+// Storage of the current substep: Wk holds w_0..w_p, Vk the raw basis slots
+// j >= 1 (raw slot 0 is w_p itself).  Without a tape both are the fixed
+// workspace; with a tape, substep k has its own regions.
+template <typename R>
+struct SubBufs {
+  R* Wk;
+  R* Vk;
+  R* Wnext;  // where y_{k+1} goes
+  __device__ __forceinline__ R* raw(int j, size_t n, int p) const {
+    return j == 0 ? Wk + (size_t)p * n : Vk + (size_t)j * n;
   }
-  __syncthreads();
-  return sh.ok;
-}
-
-// Grid reduction of K per-thread partials, then a barrier.  The last block
-// to arrive sums the block partials in block order, stores them in
-// ctrl->red[], runs post(ctrl) on its thread 0, and releases the barrier.
-template <int K, class A, class Post>
-__device__ bool grid_reduce(const A& a, Shared& sh, double (&v)[K], int phase, Post post) {
-  block_sum<K>(v, sh.red);
-  if (threadIdx.x == 0) {
-    for (int k = 0; k < K; ++k) a.part[(size_t)sh.gb * NRED + k] = v[k];
-    bool last;
-    sh.gen = bar_arrive(a.sync, sh.gn, &last);
-    sh.last = last;
-  }
-  __syncthreads();
-  if (sh.last) {
-    double tot[K];
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      double s = 0.0;
-      for (int b = threadIdx.x; b < sh.gn; b += blockDim.x) s += a.part[(size_t)b * NRED + k];
-      tot[k] = s;
-    }
-    block_sum<K>(tot, sh.red);
-    if (threadIdx.x == 0) {
-      volatile PhiCtrl* vc = a.ctrl;
-      for (int k = 0; k < K; ++k) vc->red[k] = tot[k];
-      post(vc);
-      bar_release(a.sync, sh.gen);
-      sh.ok = ld_volatile_int(&a.sync->abort) == 0;
-    }
-  } else if (threadIdx.x == 0) {
-    bool ok = bar_wait(a.sync, sh.gen, SWE_ERR_TIMEOUT);
-    sh.ok = ok && (ld_volatile_int(&a.sync->abort) == 0);
-  }
-  if (threadIdx.x == 0) phase_tick(a, sh, phase);
-  __syncthreads();
-  return sh.ok;
-}
-
-template <class A>
-__device__ __forceinline__ void abort_launch(const A& a, int code) {
-  atomicCAS(&a.sync->abort, 0, code);
-}
+};
 
 template <typename R>
-__device__ __forceinline__ R* raw_slot(const PhiArgsT<R>& a, int j) {
+__device__ __forceinline__ SubBufs<R> sub_bufs(const PhiArgsT<R>& a, int k) {
   const size_t n = (size_t)4 * a.T.ng;
-  return j == 0 ? a.W + (size_t)a.p * n : a.Vbuf + (size_t)j * n;
+  SubBufs<R> b;
+  if (a.tapeW) {
+    const size_t reg = (size_t)(a.p + 1) * n;
+    b.Wk = a.tapeW + (size_t)k * reg;
+    b.Vk = a.tapeV + a.tape_offV[k];
+    b.Wnext = a.tapeW + (size_t)(k + 1) * reg;
+  } else {
+    b.Wk = a.W;
+    b.Vk = a.Vbuf;
+    b.Wnext = a.W;
+  }
+  return b;
+}
+
+__device__ __forceinline__ int taylor_steps(double hnorm) {
+  return (int)fmax(1.0, ceil(hnorm / TAYLOR_THETA));
 }
 
 // ---------------------------------------------------------------------------
@@ -185,7 +101,7 @@ constexpr int TAYLOR_TERMS = 32;
 __device__ void taylor_phi(Shared& sh, int m, int p, double tau, double hnorm) {
   const int r = threadIdx.x;
   const int M = m + p + 1;
-  const int s = (int)fmax(1.0, ceil(hnorm / TAYLOR_THETA));
+  const int s = taylor_steps(hnorm);
   // row r of (tau H): coefficients held in registers
   double cd = 0.0, cl = 0.0, cu = 0.0;
   if (r < m) {
@@ -322,6 +238,28 @@ __device__ void decide(const A& a, Shared& sh) {
       for (int r = lane; r < m_use; r += blockDim.x) C->cV[r] = tp * beta * sh.y[r] * C->sig[r];
       if (lane == 0)
         C->cV[m_use] = hnext != 0.0 ? tp * beta * tau_k * hnext * sh.x[m_use - 1] * C->sig[m_use] : 0.0;
+    }
+    if (a.tape_sub) {  // keep what the adjoint needs of this substep
+      TapeSub& S = a.tape_sub[C->n_sub];
+      if (beta > 0.0)
+        for (int r = lane; r <= m_use; r += blockDim.x) {
+          S.sig[r] = C->sig[r];
+          S.hd[r] = sh.hd[r];
+          S.hu[r] = sh.hu[r];
+          S.hl[r] = sh.hl[r];
+        }
+      if (lane == 0) {
+        S.t = t;
+        S.tau = tau_k;
+        S.beta = beta;
+        S.hnext = hnext;
+        S.m = m_use;
+        S.s = beta > 0.0 ? taylor_steps(hnorm) : 0;
+        S.land = land;
+        S.out_idx = C->out_idx;
+        S.broken = (beta > 0.0 && C->broken && m_use == C->size) ? 1 : 0;
+        for (int j = 0; j <= PMAX; ++j) S.wnz[j] = j <= p ? C->wnz[j] : 0;
+      }
     }
   }
   __syncthreads();
@@ -468,7 +406,7 @@ __device__ bool phi_run(const PhiArgsT<R>& a, Shared& sh) {
       for (int c = 0; c < 4; ++c) {
         const size_t e = (size_t)c * ng + i;
         R yv0 = a.v[0] ? ld(a.v[0] + e) : R(0);
-        a.W[e] = yv0;
+        (a.tapeW ? a.tapeW : a.W)[e] = yv0;
         nz0 += (yv0 != R(0)) ? 1 : 0;
         for (int l = 0; l <= p; ++l)
           if (a.v[l]) {
@@ -509,10 +447,22 @@ __device__ bool phi_run(const PhiArgsT<R>& a, Shared& sh) {
 
   for (int oi = 0; oi < a.ns; ++oi) {
     const double t_out = a.rho[oi];
-    if (sh.gb == 0 && threadIdx.x == 0) C->t_out = t_out;
+    if (sh.gb == 0 && threadIdx.x == 0) {
+      C->t_out = t_out;
+      C->out_idx = oi;
+    }
     while (vld(&C->t) < t_out) {
       // ---- step 1: w_j = A w_{j-1} + sum_l t^l/l! v_{j+l}  (Eq. eq3.18) ----
       const double t = vld(&C->t);
+      const int ksub = vldi(&C->n_sub);
+      if (a.tapeW && ksub >= a.tape_cap) {  // uniform: every block sees the same count
+        if (sh.gb == 0 && threadIdx.x == 0) {
+          C->status = SWE_ERR_INVALID_ARG;
+          abort_launch(a, SWE_ERR_INVALID_ARG);
+        }
+        return false;
+      }
+      const SubBufs<R> B = sub_bufs(a, ksub);
       for (int j = 1; j <= p; ++j) {
         double cl[PMAX + 1];
         {
@@ -526,8 +476,8 @@ __device__ bool phi_run(const PhiArgsT<R>& a, Shared& sh) {
           }
         }
         const bool nz_prev = vldi(&C->wnz[j - 1]) != 0;
-        R* wprev = a.W + (size_t)(j - 1) * n;
-        R* wj = a.W + (size_t)j * n;
+        R* wprev = B.Wk + (size_t)(j - 1) * n;
+        R* wj = B.Wk + (size_t)j * n;
         if (nz_prev) {
           FOR_CELLS(i)
             pass1_cell<MODE_J>(T, i, wprev, R(1), a.u_lin, a.tmp, a.tmp + (size_t)4 * ng);
@@ -595,9 +545,9 @@ __device__ bool phi_run(const PhiArgsT<R>& a, Shared& sh) {
           R* SQ = a.tmp + (size_t)4 * ng;
           while (vldi(&C->size) < m_req && !vldi(&C->broken)) {
             const int j = vldi(&C->size);
-            R* rj = raw_slot(a, j);
-            R* rj1 = raw_slot(a, j + 1);
-            R* rjm = j > 0 ? raw_slot(a, j - 1) : nullptr;
+            R* rj = B.raw(j, n, p);
+            R* rj1 = B.raw(j + 1, n, p);
+            R* rjm = j > 0 ? B.raw(j - 1, n, p) : nullptr;
             R* Lj = a.Lring + (size_t)(j % 3) * n;
             R* Ljm = a.Lring + (size_t)((j + 2) % 3) * n;
             R* Lj1 = a.Lring + (size_t)((j + 1) % 3) * n;
@@ -682,9 +632,9 @@ __device__ bool phi_run(const PhiArgsT<R>& a, Shared& sh) {
           for (int c = 0; c < 4; ++c) {
             const size_t e = (size_t)c * ng + i;
             R y = R(0);
-            for (int j = 0; j < p; ++j) y = fma(shared_coef<R>(sh, KMAX + 2 + j), a.W[(size_t)j * n + e], y);
-            for (int r = 0; r < ncomb; ++r) y = fma(shared_coef<R>(sh, r), raw_slot(a, r)[e], y);
-            a.W[e] = y;
+            for (int j = 0; j < p; ++j) y = fma(shared_coef<R>(sh, KMAX + 2 + j), B.Wk[(size_t)j * n + e], y);
+            for (int r = 0; r < ncomb; ++r) y = fma(shared_coef<R>(sh, r), B.raw(r, n, p)[e], y);
+            B.Wnext[e] = y;
             if (yo) yo[e] = y;
             nzy += (y != R(0)) ? 1 : 0;
           }

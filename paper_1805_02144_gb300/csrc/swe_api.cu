@@ -13,11 +13,14 @@
 #include <vector>
 
 #include "../../include/swe_exprb.h"
+#include "adj_args.h"
 #include "grid_build.h"
 #include "phi_args.h"
 #include "swe_dev.cuh"
 
 namespace swe {
+int adj_max_blocks(int* nblocks, int* threads);
+int launch_adj_kernel(const AdjArgs& a, int nblocks, cudaStream_t st);
 template <class A>
 int launch_phi_kernel(const PhiLaunch& L, const A& a, cudaStream_t stream);
 int phi_select(int ng, int single, PhiLaunch* out);
@@ -91,6 +94,15 @@ struct swe_grid {
   size_t ev_used = 0;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> phi_ev, call_ev;
   int64_t kernel_launches = 0;
+  // adjoint (created on first use)
+  void* dadj = nullptr;
+  int adj_nblocks = 0;
+  double *aY = nullptr, *aWb = nullptr, *aX = nullptr, *aP = nullptr, *aPL = nullptr, *aZb = nullptr,
+         *apart = nullptr, *apartw = nullptr, *axs = nullptr, *avec = nullptr;
+  AdjCtrl* actrl = nullptr;
+  void* dtape = nullptr;     // tapes of the recorded forward calls (grown on demand)
+  size_t tape_bytes = 0;
+  int adj_status_host = 0;
 };
 
 struct swe_ensemble {
@@ -155,15 +167,19 @@ __global__ void k_pass1T(Tables T, const double* lam, const double* aux, double*
     pass1T_cell<MODE>(T, i, lam, aux, t);
 }
 
+// out = alpha * stencil (accumulate = 0) or out += alpha * stencil
 template <int MODE>
 __global__ void k_pass2T(Tables T, const double* lam, const double* u, const double* aux, const double* t,
-                         double* out) {
+                         double alpha, int accumulate, double* out) {
   const int ng = T.ng;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ng; i += gridDim.x * blockDim.x) {
     double o[4];
     pass2T_cell<MODE>(T, i, lam, u, aux, t, o);
 #pragma unroll
-    for (int c = 0; c < 4; ++c) out[(size_t)c * ng + i] = o[c];
+    for (int c = 0; c < 4; ++c) {
+      const size_t e = (size_t)c * ng + i;
+      out[e] = accumulate ? fma(alpha, o[c], out[e]) : alpha * o[c];
+    }
   }
 }
 
@@ -432,6 +448,31 @@ int resolve_opts(const phi_opts* in, phi_opts& o) {
   return SWE_OK;
 }
 
+// Offsets of each call's records in a step's replay array: the landing rule
+// of Algorithm 1 (R9 of the oracle) run over the records, call by call, with
+// the outputs rho of each call.
+int replay_split(const double* rec, int nrec, const std::vector<std::vector<double>>& rhos,
+                 std::vector<int>& offs) {
+  int pos = 0;
+  for (size_t c = 0; c < rhos.size(); ++c) {
+    offs[c] = pos;
+    double t = 0.0;
+    for (double rho : rhos[c]) {
+      while (t < rho) {
+        if (pos >= nrec) return fail(SWE_ERR_INVALID_ARG, "replay: too few records for the scheme's calls");
+        const double tau = rec[3 * pos];
+        const bool acc = rec[3 * pos + 2] != 0.0;
+        ++pos;
+        if (!(tau > 0.0)) return fail(SWE_ERR_INVALID_ARG, "replay: non-positive step size");
+        const double remaining = rho - t;
+        const bool land = tau >= remaining * (1.0 - 1e-12);
+        if (acc) t = land ? rho : t + tau;
+      }
+    }
+  }
+  return SWE_OK;
+}
+
 int stage_replay(swe_grid* g, const phi_opts& o, cudaStream_t st) {
   if (!o.replay) return SWE_OK;
   if (o.n_replay > g->replay_cap) {
@@ -493,9 +534,19 @@ int prepare_lin(swe_grid* g, const double* u_lin, const phi_opts& o, cudaStream_
 }
 
 // One phipm_simul_iom2 evaluation; prepare_lin(u_lin) must precede it on the stream.
+// Tape of one recorded call (device pointers inside swe_grid::dtape).
+struct TapeCall {
+  double* W = nullptr;
+  double* V = nullptr;
+  long long* offV = nullptr;
+  TapeSub* sub = nullptr;
+  int K = 0;  // accepted substeps
+  int p = 0;
+};
+
 int phi_call(swe_grid* g, const double* u_lin, double dt, int p, const double* const* v, int ns,
              const double* rho, double* const* y_out, const phi_opts& o, int call_index, int* m_slot,
-             int replay_offset, cudaStream_t st) {
+             int replay_offset, cudaStream_t st, const TapeCall* tape = nullptr) {
   CK(cudaMemsetAsync(g->sync, 0, sizeof(GridSync), st));
   if (o.precision == 0) {
     PhiArgs a{};
@@ -510,6 +561,13 @@ int phi_call(swe_grid* g, const double* u_lin, double dt, int p, const double* c
     a.Lring = g->Lring;
     a.Zbuf = g->Zbuf;
     fill_phi_args(g, a, dt, p, ns, rho, o, call_index, m_slot, replay_offset);
+    if (tape) {
+      a.tapeW = tape->W;
+      a.tapeV = tape->V;
+      a.tape_offV = tape->offV;
+      a.tape_sub = tape->sub;
+      a.tape_cap = tape->K;
+    }
     ProfSpan span(g, st, &g->phi_ev);
     int e = launch_phi_kernel(g->launch, a, st);
     if (e != 0) return cuda_fail((cudaError_t)e, "cudaLaunchCooperativeKernel(phi_kernel)");
@@ -585,6 +643,209 @@ int read_stats(swe_grid* g, phi_stats* stats, cudaStream_t st) {
     }
     stats->n_trace = k;
   }
+  return SWE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// adjoint of a step (exprb_step_adjoint)
+// ---------------------------------------------------------------------------
+constexpr int ADJ_XS_STEPS = 4096;  // scaling steps of one exponential the scratch holds
+constexpr int ADJ_VECS = 6;         // scheme-level vectors of the adjoint driver
+
+int ensure_adjoint(swe_grid* g) {
+  if (g->dadj) return SWE_OK;
+  int nb = 0, thr = 0;
+  if (adj_max_blocks(&nb, &thr) != 0) return fail(SWE_ERR_CUDA, "occupancy query for adj_kernel failed");
+  const size_t ng = g->T.ng, n = 4 * ng;
+  const size_t mw = KMAX + PMAX + 2;
+  size_t sizes[] = {n * 8,                                      // Y
+                    (size_t)(PMAX + 1) * n * 8,                 // Wb
+                    2 * n * 8,                                  // X
+                    2 * n * 8,                                  // P
+                    10 * ng * 8,                                // PL
+                    n * 8,                                      // Zb
+                    (size_t)nb * NRED * 8,                      // part
+                    (size_t)nb * ADJ_KW * 8,                    // partw
+                    (size_t)(ADJ_XS_STEPS + 40) * mw * 8,       // xs
+                    (size_t)ADJ_VECS * n * 8,                   // scheme vectors
+                    sizeof(AdjCtrl)};
+  void** dst[] = {(void**)&g->aY,   (void**)&g->aWb,    (void**)&g->aX,  (void**)&g->aP,
+                  (void**)&g->aPL,  (void**)&g->aZb,    (void**)&g->apart, (void**)&g->apartw,
+                  (void**)&g->axs,  (void**)&g->avec,   (void**)&g->actrl};
+  constexpr int NP = sizeof(sizes) / sizeof(sizes[0]);
+  static_assert(NP == 11, "adjoint workspace layout");
+  size_t total = 0;
+  for (size_t x : sizes) total += (x + 255) & ~size_t(255);
+  cudaError_t e = cudaMalloc(&g->dadj, total);
+  if (e != cudaSuccess) {
+    g->dadj = nullptr;
+    return fail(SWE_ERR_NOMEM, std::string("adjoint workspace allocation failed: ") + cudaGetErrorString(e));
+  }
+  char* q = (char*)g->dadj;
+  for (int k = 0; k < NP; ++k) {
+    *dst[k] = q;
+    q += (sizes[k] + 255) & ~size_t(255);
+  }
+  g->adj_nblocks = nb;
+  CK(cudaMemset(g->dadj, 0, total));
+  return SWE_OK;
+}
+
+// Splits a step's trace into calls and lays the tapes out: per call, the
+// accepted substeps and, per substep, the largest Krylov size of its
+// attempts (the basis the replay builds).  Fills `replay` with the calls'
+// (tau, m, accepted) records in call order and `first` with each call's
+// offset into it.
+struct TapePlan {
+  std::vector<double> replay;
+  std::vector<int> first, count;
+  std::vector<std::vector<int>> mmax;  // per call, per accepted substep
+};
+
+int plan_tape(const phi_attempt* trace, int n_trace, int ncalls, TapePlan& P) {
+  P.first.assign(ncalls, 0);
+  P.count.assign(ncalls, 0);
+  P.mmax.assign(ncalls, {});
+  P.replay.clear();
+  int pos = 0;
+  for (int c = 0; c < ncalls; ++c) {
+    P.first[c] = (int)(P.replay.size() / 3);
+    int cur = 0;
+    bool open = false;
+    while (pos < n_trace && trace[pos].call == c) {
+      const phi_attempt& r = trace[pos++];
+      if (r.m < 1 || r.m > KMAX || !(r.tau > 0.0)) return fail(SWE_ERR_INVALID_ARG, "trace: invalid attempt");
+      P.replay.push_back(r.tau);
+      P.replay.push_back((double)r.m);
+      P.replay.push_back(r.accepted ? 1.0 : 0.0);
+      cur = std::max(cur, r.m);
+      open = true;
+      if (r.accepted) {
+        P.mmax[c].push_back(cur);
+        cur = 0;
+        open = false;
+      }
+    }
+    P.count[c] = (int)(P.replay.size() / 3) - P.first[c];
+    if (open) return fail(SWE_ERR_INVALID_ARG, "trace: a call ends with a rejected attempt");
+    if (P.mmax[c].empty()) return fail(SWE_ERR_INVALID_ARG, "trace: a call has no accepted substep");
+  }
+  if (pos != n_trace) return fail(SWE_ERR_INVALID_ARG, "trace: call indices do not match the scheme");
+  return SWE_OK;
+}
+
+int alloc_tapes(swe_grid* g, const TapePlan& P, const int* pc, int ncalls, TapeCall* out, cudaStream_t st) {
+  const size_t n = (size_t)4 * g->T.ng;
+  auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+  size_t total = 0;
+  std::vector<size_t> offW(ncalls), offV(ncalls), offO(ncalls), offS(ncalls);
+  for (int c = 0; c < ncalls; ++c) {
+    const size_t K = P.mmax[c].size();
+    size_t vsz = 0;
+    for (int m : P.mmax[c]) vsz += (size_t)(m + 1) * n;
+    offW[c] = total;
+    total += al((K + 1) * (size_t)(pc[c] + 1) * n * 8);
+    offV[c] = total;
+    total += al(vsz * 8);
+    offO[c] = total;
+    total += al(K * sizeof(long long));
+    offS[c] = total;
+    total += al(K * sizeof(TapeSub));
+  }
+  if (total > g->tape_bytes) {
+    if (g->dtape) {
+      CK(cudaStreamSynchronize(st));
+      cudaFree(g->dtape);
+    }
+    g->dtape = nullptr;
+    g->tape_bytes = 0;
+    cudaError_t e = cudaMalloc(&g->dtape, total);
+    if (e != cudaSuccess) {
+      g->dtape = nullptr;
+      return fail(SWE_ERR_NOMEM, std::string("tape allocation failed: ") + cudaGetErrorString(e));
+    }
+    g->tape_bytes = total;
+  }
+  char* base = (char*)g->dtape;
+  for (int c = 0; c < ncalls; ++c) {
+    TapeCall& t = out[c];
+    t.W = (double*)(base + offW[c]);
+    t.V = (double*)(base + offV[c]);
+    t.offV = (long long*)(base + offO[c]);
+    t.sub = (TapeSub*)(base + offS[c]);
+    t.K = (int)P.mmax[c].size();
+    t.p = pc[c];
+    std::vector<long long> o(t.K);
+    long long acc = 0;
+    for (int k = 0; k < t.K; ++k) {
+      o[k] = acc;
+      acc += (long long)(P.mmax[c][k] + 1) * (long long)n;
+    }
+    CK(cudaMemcpyAsync(t.offV, o.data(), o.size() * sizeof(long long), cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));  // o is released on return
+  }
+  return SWE_OK;
+}
+
+// Reverse of one recorded call: vbar[l] += ..., ubar += ...
+int adj_call(swe_grid* g, const TapeCall& tp, const double* u_lin, double dt, const double* const* ybar,
+             int ns, double* const* vbar, double* ubar, cudaStream_t st) {
+  CK(cudaMemsetAsync(g->sync, 0, sizeof(GridSync), st));
+  CK(cudaMemsetAsync(g->actrl, 0, sizeof(AdjCtrl), st));
+  AdjArgs a{};
+  a.T = g->T;
+  a.u_lin = u_lin;
+  a.aux = g->aux;
+  a.dt = dt;
+  a.p = tp.p;
+  a.nsub = tp.K;
+  for (int i = 0; i < ns; ++i) a.ybar[i] = ybar[i];
+  for (int l = 0; l <= tp.p; ++l) a.vbar[l] = vbar[l];
+  a.ubar = ubar;
+  a.tapeW = tp.W;
+  a.tapeV = tp.V;
+  a.tape_offV = tp.offV;
+  a.tape_sub = tp.sub;
+  a.Y = g->aY;
+  a.Wb = g->aWb;
+  a.X = g->aX;
+  a.P = g->aP;
+  a.PL = g->aPL;
+  a.Zb = g->aZb;
+  a.part = g->apart;
+  a.partw = g->apartw;
+  a.xs = g->axs;
+  a.xs_steps = ADJ_XS_STEPS;
+  a.ctrl = g->actrl;
+  a.sync = g->sync;
+  a.prof = nullptr;
+  int e = launch_adj_kernel(a, g->adj_nblocks, st);
+  if (e != 0) return cuda_fail((cudaError_t)e, "cudaLaunchCooperativeKernel(adj_kernel)");
+  count_launches(g, 1);
+  CK(cudaMemcpyAsync(&g->adj_status_host, &g->actrl->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (g->adj_status_host != SWE_OK) return fail(g->adj_status_host, "adj_kernel reported an error");
+  return SWE_OK;
+}
+
+// out = (accumulate ? out : 0) + alpha * J(u)^T lam (MODE_JT, aux of u in
+// g->aux) or alpha * (J(x) - J(0))^T lam (MODE_QT, aux of x written to auxq).
+template <int MODE>
+int run_transposed(swe_grid* g, const double* u, const double* lam, double alpha, int accumulate, double* out,
+                   double* auxq, cudaStream_t st) {
+  Tables T = g->T;
+  const int nb = grid_blocks(T.ng);
+  const double* aux = g->aux;
+  if (MODE == MODE_QT) {
+    T.two_omega = 0.0;
+    k_aux<double><<<nb, TPB, 0, st>>>(T, u, auxq);
+    count_launches(g, 1);
+    aux = auxq;
+  }
+  k_pass1T<MODE><<<nb, TPB, 0, st>>>(T, lam, aux, g->tmp2);
+  k_pass2T<MODE><<<nb, TPB, 0, st>>>(T, lam, u, aux, g->tmp2, alpha, accumulate, out);
+  CK(cudaGetLastError());
+  count_launches(g, 2);
   return SWE_OK;
 }
 
@@ -699,6 +960,8 @@ void swe_destroy_grid(swe_grid* g) {
   if (g->dtabF) cudaFree(g->dtabF);
   if (g->dwsF) cudaFree(g->dwsF);
   if (g->replay) cudaFree(g->replay);
+  if (g->dadj) cudaFree(g->dadj);
+  if (g->dtape) cudaFree(g->dtape);
   delete g;
 }
 
@@ -758,7 +1021,7 @@ int swe_jtv(const swe_grid* gc, const double* u, const double* lam, double* out,
   int nb = grid_blocks(T.ng);
   k_aux<double><<<nb, TPB, 0, st>>>(T, u, g->aux);
   k_pass1T<MODE_JT><<<nb, TPB, 0, st>>>(T, lam, g->aux, g->tmp2);
-  k_pass2T<MODE_JT><<<nb, TPB, 0, st>>>(T, lam, u, g->aux, g->tmp2, out);
+  k_pass2T<MODE_JT><<<nb, TPB, 0, st>>>(T, lam, u, g->aux, g->tmp2, 1.0, 0, out);
   CK(cudaGetLastError());
   count_launches(g, 3);
   return SWE_OK;
@@ -776,7 +1039,7 @@ int swe_dqtv(const swe_grid* gc, const double* x, const double* lam, double* out
   int nb = grid_blocks(T0.ng);
   k_aux<double><<<nb, TPB, 0, st>>>(T0, x, g->aux);
   k_pass1T<MODE_QT><<<nb, TPB, 0, st>>>(T0, lam, g->aux, g->tmp2);
-  k_pass2T<MODE_QT><<<nb, TPB, 0, st>>>(T0, lam, x, g->aux, g->tmp2, out);
+  k_pass2T<MODE_QT><<<nb, TPB, 0, st>>>(T0, lam, x, g->aux, g->tmp2, 1.0, 0, out);
   CK(cudaGetLastError());
   count_launches(g, 3);
   return SWE_OK;
@@ -860,50 +1123,69 @@ int exprb_step(swe_grid* g, int scheme, double dt, const double* u_n, double* u_
   auto slot = [&](int k) { return slots ? slots + k : nullptr; };
   int call = 0;
   // Replay records are consumed call by call; the device keeps its own count
-  // per launch, so the host offsets each call by the attempts already used.
-  // Replay is supported for single-call schemes and for phi_action only.
-  if (o.replay && scheme != SWE_EPI2 && !(scheme == SWE_EPI3 && !state->have_prev))
-    return fail(SWE_ERR_INVALID_ARG, "replay is supported by phi_action and EPI2 steps");
+  // per launch, so the host offsets each call by the attempts it consumes
+  // (found by running the landing rule over the records).
+  std::vector<int> roff(4, 0);
+  if (o.replay) {
+    std::vector<std::vector<double>> rhos;
+    if (scheme == SWE_EPI2 || scheme == SWE_EPI3)
+      rhos = {{1.0}};
+    else if (scheme == SWE_EXPRB42)
+      rhos = {{0.75}, {1.0}};
+    else if (scheme == SWE_PEXPRB43)
+      rhos = {{0.5, 1.0}, {1.0}};
+    else
+      rhos = {{0.5, 0.9}, {0.5, 0.9}, {1.0}};
+    if ((rc = replay_split(o.replay, o.n_replay, rhos, roff))) return rc;
+  }
+  auto roff_at = [&](int c) { return roff[c]; };
   const double one = 1.0;
   if (scheme == SWE_EPI2 || (scheme == SWE_EPI3 && !state->have_prev)) {
     const double* v[2] = {nullptr, vF};
     double* y[1] = {B[1]};
-    if ((rc = phi_call(g, u_n, dt, 1, v, 1, &one, y, o, call++, slot(0), 0, st))) return rc;
+    if ((rc = phi_call(g, u_n, dt, 1, v, 1, &one, y, o, call, slot(0), roff_at(call), st))) return rc;
+    ++call;
     if ((rc = run_lincomb(g, u_np1, {{1.0, u_n}, {1.0, B[1]}}, st))) return rc;
   } else if (scheme == SWE_EXPRB42) {
     const double r1 = 0.75;
     const double* v1[2] = {nullptr, vF};
     double* y1[1] = {B[1]};
-    if ((rc = phi_call(g, u_n, dt, 1, v1, 1, &r1, y1, o, call++, slot(1), 0, st))) return rc;
+    if ((rc = phi_call(g, u_n, dt, 1, v1, 1, &r1, y1, o, call, slot(1), roff_at(call), st))) return rc;
+    ++call;
     // D_2 = N(U_2) - N(u_n) = Q(U_2 - u_n); v_3 = (32/9) dt D_2
     if ((rc = run_quad(g, B[1], B[2], (32.0 / 9.0) * dt, st))) return rc;
     const double* v2[4] = {nullptr, vF, nullptr, B[2]};
     double* y2[1] = {B[3]};
-    if ((rc = phi_call(g, u_n, dt, 3, v2, 1, &one, y2, o, call++, slot(2), 0, st))) return rc;
+    if ((rc = phi_call(g, u_n, dt, 3, v2, 1, &one, y2, o, call, slot(2), roff_at(call), st))) return rc;
+    ++call;
     if ((rc = run_lincomb(g, u_np1, {{1.0, u_n}, {1.0, B[3]}}, st))) return rc;
   } else if (scheme == SWE_PEXPRB43) {
     const double r1[2] = {0.5, 1.0};
     const double* v1[2] = {nullptr, vF};
     double* y1[2] = {B[1], B[2]};
-    if ((rc = phi_call(g, u_n, dt, 1, v1, 2, r1, y1, o, call++, slot(1), 0, st))) return rc;
+    if ((rc = phi_call(g, u_n, dt, 1, v1, 2, r1, y1, o, call, slot(1), roff_at(call), st))) return rc;
+    ++call;
     if ((rc = run_quad(g, B[1], B[3], dt, st))) return rc;  // dt D_2
     if ((rc = run_quad(g, B[2], B[4], dt, st))) return rc;  // dt D_3
     if ((rc = run_lincomb(g, B[5], {{16.0, B[3]}, {-2.0, B[4]}}, st))) return rc;
     if ((rc = run_lincomb(g, B[6], {{-48.0, B[3]}, {12.0, B[4]}}, st))) return rc;
     const double* v2[5] = {nullptr, nullptr, nullptr, B[5], B[6]};
     double* y2[1] = {B[7]};
-    if ((rc = phi_call(g, u_n, dt, 4, v2, 1, &one, y2, o, call++, slot(2), 0, st))) return rc;
+    if ((rc = phi_call(g, u_n, dt, 4, v2, 1, &one, y2, o, call, slot(2), roff_at(call), st))) return rc;
+    ++call;
     // u_{n+1} = U_3 + w = u_n + Y(1) + w
     if ((rc = run_lincomb(g, u_np1, {{1.0, u_n}, {1.0, B[2]}, {1.0, B[7]}}, st))) return rc;
   } else if (scheme == SWE_EXPRB53) {
     const double r1[2] = {0.5, 0.9};
     const double* v1[2] = {nullptr, vF};
     double* y1[2] = {B[1], B[2]};
-    if ((rc = phi_call(g, u_n, dt, 1, v1, 2, r1, y1, o, call++, slot(1), 0, st))) return rc;
+    if ((rc = phi_call(g, u_n, dt, 1, v1, 2, r1, y1, o, call, slot(1), roff_at(call), st))) return rc;
+    ++call;
     if ((rc = run_quad(g, B[1], B[3], dt, st))) return rc;  // dt D_2
     const double* v2[4] = {nullptr, nullptr, nullptr, B[3]};
     double* y2[2] = {B[4], B[5]};
-    if ((rc = phi_call(g, u_n, dt, 3, v2, 2, r1, y2, o, call++, slot(2), 0, st))) return rc;
+    if ((rc = phi_call(g, u_n, dt, 3, v2, 2, r1, y2, o, call, slot(2), roff_at(call), st))) return rc;
+    ++call;
     // U_3 - u_n = Y_1(9/10) + (27/25)/(1/2)^3 Y_3(1/2) + (729/125)/(9/10)^3 Y_3(9/10)
     const double c3h = (27.0 / 25.0) / (0.5 * 0.5 * 0.5);
     const double c3n = (729.0 / 125.0) / (0.9 * 0.9 * 0.9);
@@ -913,7 +1195,8 @@ int exprb_step(swe_grid* g, int scheme, double dt, const double* u_n, double* u_
     if ((rc = run_lincomb(g, B[9], {{-60.0, B[3]}, {500.0 / 27.0, B[7]}}, st))) return rc;
     const double* v3[5] = {nullptr, vF, nullptr, B[8], B[9]};
     double* y3[1] = {B[10]};
-    if ((rc = phi_call(g, u_n, dt, 4, v3, 1, &one, y3, o, call++, slot(3), 0, st))) return rc;
+    if ((rc = phi_call(g, u_n, dt, 4, v3, 1, &one, y3, o, call, slot(3), roff_at(call), st))) return rc;
+    ++call;
     if ((rc = run_lincomb(g, u_np1, {{1.0, u_n}, {1.0, B[10]}}, st))) return rc;
   } else {  // SWE_EPI3 with history
     // R_{n-1} = F(u_{n-1}) - F(u_n) - J_n (u_{n-1} - u_n) = Q(u_{n-1} - u_n); v_2 = (2/3) dt R
@@ -921,7 +1204,8 @@ int exprb_step(swe_grid* g, int scheme, double dt, const double* u_n, double* u_
     if ((rc = run_quad(g, B[1], B[2], (2.0 / 3.0) * dt, st))) return rc;
     const double* v[3] = {nullptr, vF, B[2]};
     double* y[1] = {B[3]};
-    if ((rc = phi_call(g, u_n, dt, 2, v, 1, &one, y, o, call++, slot(1), 0, st))) return rc;
+    if ((rc = phi_call(g, u_n, dt, 2, v, 1, &one, y, o, call, slot(1), roff_at(call), st))) return rc;
+    ++call;
     if ((rc = run_lincomb(g, u_np1, {{1.0, u_n}, {1.0, B[3]}}, st))) return rc;
   }
   if (scheme == SWE_EPI3) {
@@ -930,6 +1214,100 @@ int exprb_step(swe_grid* g, int scheme, double dt, const double* u_n, double* u_
   }
   span.finish();
   return read_stats(g, stats, st);
+}
+
+int exprb_step_adjoint(swe_grid* g, int scheme, double dt, const double* u_n, const phi_attempt* trace,
+                       int n_trace, const double* lam_np1, double* lam_n, const phi_opts* opts,
+                       phi_stats* stats, void* stream) {
+  if (!g || !u_n || !trace || !lam_np1 || !lam_n)
+    return fail(SWE_ERR_INVALID_ARG, "exprb_step_adjoint: NULL argument");
+  if (lam_n == lam_np1 || lam_n == u_n) return fail(SWE_ERR_INVALID_ARG, "exprb_step_adjoint: lam_n must not alias");
+  if (scheme != SWE_EPI2 && scheme != SWE_EXPRB42)
+    return fail(SWE_ERR_INVALID_ARG, "exprb_step_adjoint: EPI2 and exprb42 are supported");
+  if (n_trace < 1) return fail(SWE_ERR_INVALID_ARG, "exprb_step_adjoint: empty trace");
+  int rc;
+  phi_opts o;
+  if ((rc = resolve_opts(opts, o))) return rc;
+  if (o.precision != 0) return fail(SWE_ERR_INVALID_ARG, "exprb_step_adjoint: FP64 only (precision = 0)");
+  if ((rc = ensure_workspace(g))) return rc;
+  if ((rc = ensure_adjoint(g))) return rc;
+  cudaStream_t st = S(stream);
+  const int ncalls = scheme == SWE_EPI2 ? 1 : 2;
+  const int pc[2] = {1, 3};
+  TapePlan P;
+  if ((rc = plan_tape(trace, n_trace, ncalls, P))) return rc;
+  TapeCall tapes[2];
+  if ((rc = alloc_tapes(g, P, pc, ncalls, tapes, st))) return rc;
+  // forward replay with tapes: the same calls as exprb_step
+  o.replay = P.replay.data();
+  o.n_replay = (int)(P.replay.size() / 3);
+  if ((rc = stage_replay(g, o, st))) return rc;
+  const size_t n = (size_t)4 * g->T.ng;
+  double* vF = g->avec;
+  double* Y1 = g->avec + n;
+  double* v3 = g->avec + 2 * n;
+  double* yw = g->avec + 3 * n;    // forward output (not needed)
+  double* VB1 = g->avec + 4 * n;   // adjoint of v_1 = dt F(u_n)
+  double* VB3 = g->avec + 5 * n;   // adjoint of v_3 (exprb42), then of Y1
+  ProfSpan span(g, st, &g->call_ev);
+  CK(cudaMemsetAsync(g->stats, 0, sizeof(DevStats), st));
+  if ((rc = prepare_lin(g, u_n, o, st))) return rc;
+  if ((rc = run_rhs(g, u_n, vF, dt, st))) return rc;
+  const double one = 1.0, r1 = 0.75;
+  if (scheme == SWE_EPI2) {
+    const double* v[2] = {nullptr, vF};
+    double* y[1] = {yw};
+    if ((rc = phi_call(g, u_n, dt, 1, v, 1, &one, y, o, 0, nullptr, P.first[0], st, &tapes[0]))) return rc;
+  } else {
+    const double* v1[2] = {nullptr, vF};
+    double* y1[1] = {Y1};
+    if ((rc = phi_call(g, u_n, dt, 1, v1, 1, &r1, y1, o, 0, nullptr, P.first[0], st, &tapes[0]))) return rc;
+    if ((rc = run_quad(g, Y1, v3, (32.0 / 9.0) * dt, st))) return rc;
+    const double* v2[4] = {nullptr, vF, nullptr, v3};
+    double* y2[1] = {yw};
+    if ((rc = phi_call(g, u_n, dt, 3, v2, 1, &one, y2, o, 1, nullptr, P.first[1], st, &tapes[1]))) return rc;
+  }
+  {
+    DevStats ds;
+    CK(cudaMemcpyAsync(&ds, g->stats, sizeof(DevStats), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (ds.status != SWE_OK) return fail(ds.status, "exprb_step_adjoint: forward replay failed");
+    if (stats) {
+      stats->n_jv = ds.n_jv;
+      stats->n_substeps = ds.n_sub;
+      stats->n_reject = ds.n_rej;
+      stats->m_last = ds.m_last;
+      stats->m_max_used = ds.m_max_used;
+      stats->status = ds.status;
+      stats->n_trace = 0;
+    }
+  }
+  // reverse: u_{n+1} = u_n + y
+  CK(cudaMemcpyAsync(lam_n, lam_np1, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemsetAsync(VB1, 0, n * sizeof(double), st));
+  if (scheme == SWE_EPI2) {
+    const double* yb[1] = {lam_np1};
+    double* vb[2] = {nullptr, VB1};
+    if ((rc = adj_call(g, tapes[0], u_n, dt, yb, 1, vb, lam_n, st))) return rc;
+  } else {
+    CK(cudaMemsetAsync(VB3, 0, n * sizeof(double), st));
+    {
+      const double* yb[1] = {lam_np1};
+      double* vb[4] = {nullptr, VB1, nullptr, VB3};
+      if ((rc = adj_call(g, tapes[1], u_n, dt, yb, 1, vb, lam_n, st))) return rc;
+    }
+    // v_3 = (32/9) dt Q(Y1): Ybar1 = (32/9) dt Q'(Y1)^T VB3 (into yw)
+    if ((rc = run_transposed<MODE_QT>(g, Y1, VB3, (32.0 / 9.0) * dt, 0, yw, v3, st))) return rc;
+    {
+      const double* yb[1] = {yw};
+      double* vb[2] = {nullptr, VB1};
+      if ((rc = adj_call(g, tapes[0], u_n, dt, yb, 1, vb, lam_n, st))) return rc;
+    }
+  }
+  // v_1 = dt F(u_n): lam_n += dt J(u_n)^T VB1
+  if ((rc = run_transposed<MODE_JT>(g, u_n, VB1, dt, 1, lam_n, nullptr, st))) return rc;
+  span.finish();
+  return SWE_OK;
 }
 
 // ---------------------------------------------------------------------------
