@@ -297,6 +297,90 @@ def batching_block() -> dict:
                                   "total": sum(st["blocks"])}}
 
 
+def adjoint_block(flush) -> dict:
+    """Gradient of the 6 h exprb42 forecast misfit (level 6, dt 1800 s, 12 steps,
+    1000 observations, sigma 5 m) by per-step checkpoints, recomputation with a
+    Krylov tape and the reverse sweep, against the forecast itself."""
+    import torch
+    from paper_1805_02144_gb300.api import Grid, SchemeState, exprb_step, exprb_step_adjoint
+    from paper_1805_02144_gb300.inputs import balanced_state, observation_network, random_vector
+    G = Grid(6)
+    x = G.cell_centres()
+    ng = G.ncells
+    dt, nsteps = 1800.0, 12
+    u0 = torch.from_numpy(balanced_state(x, 2, 400.0)).cuda()
+    cells, y, sigma = observation_network(x, 1000, 7, 5.0)
+    cells_t = torch.from_numpy(cells).cuda()
+    y_t = torch.from_numpy(y).cuda()
+    opts = {"tol": TOL}
+
+    def forecast(trace: bool):
+        st = SchemeState(G)
+        u, states, traces = u0, [u0], []
+        for _ in range(nsteps):
+            if trace:
+                u, info = exprb_step(G, "exprb42", dt, u, state=st, opts=opts, stats=True, trace_cap=4096)
+                traces.append(info["trace"])
+            else:
+                u = exprb_step(G, "exprb42", dt, u, state=st, opts=opts)
+            states.append(u)
+        return states, traces
+
+    def misfit(u):
+        r = (u[3 * ng:][cells_t] - y_t) / sigma
+        lam = torch.zeros_like(u)
+        lam.index_add_(0, 3 * ng + cells_t, r / sigma)
+        return 0.5 * float(torch.dot(r, r)), lam
+
+    def gradient(states, traces):
+        J, lam = misfit(states[-1])
+        for k in reversed(range(nsteps)):
+            lam = exprb_step_adjoint(G, "exprb42", dt, states[k], traces[k], lam, opts=opts)
+        return J, lam
+
+    def timed(fn, reps=3):
+        best, out = None, None
+        for rep in range(reps):
+            flush.fill_(float(rep))  # 256 MB write: L2 (129 MB) holds nothing of the last run
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            out = fn()
+            b.record()
+            torch.cuda.synchronize()
+            t = a.elapsed_time(b)
+            best = t if best is None else min(best, t)
+        return best, out
+
+    states, traces = forecast(True)
+    gradient(states, traces)
+    fwd_ms, _ = timed(lambda: forecast(False))
+    fwdt_ms, (states, traces) = timed(lambda: forecast(True))
+    adj_ms, (J, g) = timed(lambda: gradient(states, traces))
+    # one central difference (eps = 1e-6) of the forecast with frozen decisions
+    rp = [{"tol": TOL, "replay": [[r["tau"], r["m"], float(r["accepted"])] for r in tr]} for tr in traces]
+
+    def J_replayed(u):
+        st = SchemeState(G)
+        for k in range(nsteps):
+            u = exprb_step(G, "exprb42", dt, u, state=st, opts=rp[k])
+        return misfit(u)[0]
+
+    d = torch.from_numpy(random_vector(G.n, 91)).cuda()
+    d[:3 * ng] *= float(u0[:3 * ng].abs().max())
+    d[3 * ng:] *= 400.0
+    eps = 1e-6
+    fd = (J_replayed(u0 + eps * d) - J_replayed(u0 - eps * d)) / (2 * eps)
+    gd = float(torch.dot(g, d))
+    return {"workload": "gradient of 0.5 sum (h - y)^2 / sigma^2 at 1000 seeded cells (sigma 5 m) after a "
+                        "6 h exprb42 forecast: level-6 grid (40962 cells), dt 1800 s, 12 steps, FP64, "
+                        "Tol 1e-8, frozen substep decisions, per-step checkpoints with recomputation",
+            "forecast_ms": fwd_ms, "forecast_with_trace_ms": fwdt_ms, "gradient_ms": adj_ms,
+            "adjoint_over_forward": adj_ms / fwd_ms,
+            "misfit": J, "fd_check": {"eps": eps, "fd": fd, "adjoint": gd, "rel_diff": abs(fd - gd) / abs(fd)},
+            "attempts_per_step": [len(t) for t in traces]}
+
+
 def gpu_arm(args) -> None:
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -401,6 +485,7 @@ def gpu_arm(args) -> None:
     if world == 1 and not args.no_extra:
         line["precision"] = precision_block(flush)
         line["batching"] = batching_block()
+        line["adjoint"] = adjoint_block(flush)
     if world == 1 and not args.no_cpu_baseline:
         try:
             res = run_oracle_subprocess(1, 0)
@@ -424,8 +509,19 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-extra", action="store_true", help="skip the precision/batching blocks")
+    ap.add_argument("--no-extra", action="store_true", help="skip the precision/batching/adjoint blocks")
+    ap.add_argument("--only", choices=["precision", "batching", "adjoint"],
+                    help="run one extra block alone and print it (for profiling)")
     args = ap.parse_args()
+    if args.only:
+        import torch
+        from paper_1805_02144_gb300 import build
+        build.build()
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+        fn = {"precision": lambda: precision_block(flush), "batching": batching_block,
+              "adjoint": lambda: adjoint_block(flush)}[args.only]
+        print(json.dumps({args.only: fn()}), flush=True)
+        return
     if args.impl == "reference":
         reference_arm(args)
     else:
