@@ -48,10 +48,17 @@ def _peaks():
 
 
 def _traffic():
-    """DRAM bytes per phi launch from the committed ncu summary (None if absent or stale)."""
+    """DRAM bytes per phi launch from the committed ncu summary; None if absent
+    or if the kernel's source files changed since the counters were taken."""
+    import hashlib
     p = os.path.join(ROOT, "profiles", "phi_kernel_traffic.json")
     try:
         d = json.load(open(p))
+        h = hashlib.sha256()
+        for f in d["source_files"]:
+            h.update(open(os.path.join(ROOT, f), "rb").read())
+        if h.hexdigest() != d["source_sha256"]:
+            return None
         return d.get("dram_bytes_per_launch")
     except Exception:
         return None
