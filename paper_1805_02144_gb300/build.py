@@ -43,8 +43,10 @@ def up_to_date() -> bool:
 
 
 def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None,
-          out_dir: str | None = None) -> str:
-    """Compile the library; `out_dir`/`extra` build a separately configured copy."""
+          out_dir: str | None = None, src_dir: str | None = None) -> str:
+    """Compile the library; `out_dir`/`extra`/`src_dir` build a separately
+    configured copy (other flags, or another copy of the sources)."""
+    csrc = CSRC if src_dir is None else src_dir
     lib = LIB if out_dir is None else os.path.join(out_dir, "libswe_exprb.so")
     bdir = BUILD if out_dir is None else out_dir
     if not force and out_dir is None and up_to_date():
@@ -55,7 +57,7 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
 
     def compile_one(src: str) -> str:
         obj = os.path.join(bdir, src + ".o")
-        cmd = [nvcc, *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [nvcc, *ARCH, *FLAGS, *extra, "-c", os.path.join(csrc, src), "-o", obj]
         if verbose:
             print(" ".join(cmd), flush=True)
         r = subprocess.run(cmd, capture_output=True, text=True)

@@ -113,26 +113,36 @@ __device__ void taylor_phi(Shared& sh, int m, int p, double tau, double hnorm) {
   double acc = (r == M - 1) ? 1.0 : 0.0;
   if (r < M) sh.x[r] = acc;
   __syncthreads();
+  // terms alternate between sh.x and sh.y: one block barrier per term
+  double* buf[2] = {sh.x, sh.y};
+  int c = 0;
   for (int step = 0; step < s; ++step) {
-    // sh.x holds the current term (starting with the vector itself)
+    // buf[c] holds the current term (starting with the vector itself)
     for (int k = 1; k <= TAYLOR_TERMS; ++k) {
+      const double* xc = buf[c];
       double v = 0.0;
       if (r < m) {
-        v = cd * sh.x[r];
-        if (r > 0) v = fma(cl, sh.x[r - 1], v);
-        if (r < m - 1) v = fma(cu, sh.x[r + 1], v);
-        if (r == 0) v += sh.x[m];
+        v = cd * xc[r];
+        if (r > 0) v = fma(cl, xc[r - 1], v);
+        if (r < m - 1) v = fma(cu, xc[r + 1], v);
+        if (r == 0) v += xc[m];
         v *= sh.ck[k];
       } else if (r < m + p) {
-        v = sh.x[r + 1] * sh.ck[k];
+        v = xc[r + 1] * sh.ck[k];
       }
-      __syncthreads();
       if (r < M) {
-        sh.x[r] = v;
+        buf[c ^ 1][r] = v;
         acc += v;
       }
       __syncthreads();
+      c ^= 1;
     }
+    // the buffer read by the last term is free again: the step's sum goes there
+    if (r < M) buf[c ^ 1][r] = acc;
+    __syncthreads();
+    c ^= 1;
+  }
+  if (c != 0) {  // leave x in sh.x
     if (r < M) sh.x[r] = acc;
     __syncthreads();
   }
@@ -210,15 +220,17 @@ __device__ void decide(const A& a, Shared& sh) {
       sh.hl[r] = C->hl[r];
     }
     __syncthreads();
-    if (lane == 0) {
+    if (lane < 32) {  // max column sum of |H_m| (max is exact in any order)
       double cs = 0.0;
-      for (int j = 0; j < m_use; ++j) {
+      for (int j = lane; j < m_use; j += 32) {
         double s = fabs(sh.hd[j]);
         if (j > 0) s += fabs(sh.hu[j - 1]);
         if (j + 1 < m_use) s += fabs(sh.hl[j + 1]);
         cs = fmax(cs, s);
       }
-      sh.scal[0] = cs;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) cs = fmax(cs, __shfl_xor_sync(0xffffffffu, cs, o));
+      if (lane == 0) sh.scal[0] = cs;
     }
     __syncthreads();
     hnorm = fmax(tau_k * sh.scal[0], 1.0);
@@ -290,14 +302,7 @@ __device__ void decide(const A& a, Shared& sh) {
   double hnorm_new = 1.0;
   if (beta > 0.0) {
     // ||tau_new Hhat||_1 = max(tau_new * max column sum of |H_m|, 1)
-    double cs = 0.0;
-    for (int j = 0; j < m_use; ++j) {
-      double s = fabs(sh.hd[j]);
-      if (j > 0) s += fabs(sh.hu[j - 1]);
-      if (j + 1 < m_use) s += fabs(sh.hl[j + 1]);
-      cs = fmax(cs, s);
-    }
-    hnorm_new = fmax(tau_new * cs, 1.0);
+    hnorm_new = fmax(tau_new * sh.scal[0], 1.0);
   }
   const double c_tau = cost_fn(tau_new, m_use, p, remaining, N, nA, hnorm_new);
   const double c_m = cost_fn(tau_k, m_new, p, remaining, N, nA, hnorm);
