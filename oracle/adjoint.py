@@ -21,8 +21,8 @@ ops, and differentiates it with torch.autograd (a library primitive):
   exponential (``torch.linalg.matrix_exp``), and the update of Eq. (eq3.17)
   with the corrected formula (reading R5).  Rejected attempts do not touch
   the result and are skipped.
-* ``step_replay``: the schemes of ``oracle.schemes`` (EPI2, exprb42) on top
-  of it, D_ni evaluated literally (Eq. (eqDni)).
+* ``step_replay``: the schemes of ``oracle.schemes`` (EPI2, exprb42,
+  pexprb43, exprb53) on top of it, D_ni evaluated literally (Eq. (eqDni)).
 * ``loss_and_gradient``: the quadratic observation misfit of a forecast and
   its gradient with respect to the initial state, stepping backwards with
   one recomputed step per checkpoint (the forward states are the checkpoints).
@@ -43,7 +43,8 @@ import torch
 from .phipm import Attempt, PhiOpts, phipm_simul_iom2
 from .schemes import KrylovPhi, step as np_step
 
-ADJOINT_SCHEMES = ("epi2", "exprb42")
+ADJOINT_SCHEMES = ("epi2", "exprb42", "pexprb43", "exprb53")
+NCALLS = {"epi2": 1, "exprb42": 2, "pexprb43": 2, "exprb53": 3}
 
 
 class _SpMV(torch.autograd.Function):
@@ -219,6 +220,23 @@ def step_replay(scheme: str, tm: TorchSWE, u_n: torch.Tensor, dt: float, calls: 
         D2 = _D(tm, u_n, u_n + y1)
         (w,) = phi_replay(Amul, [1.0], [None, v, None, (32.0 / 9.0) * dt * D2], calls[1])
         return u_n + w
+    if scheme == "pexprb43":
+        y_half, y_one = phi_replay(Amul, [0.5, 1.0], [None, v], calls[0])
+        U2, U3 = u_n + y_half, u_n + y_one
+        D2, D3 = _D(tm, u_n, U2), _D(tm, u_n, U3)
+        (w,) = phi_replay(Amul, [1.0], [None, None, None, dt * (16.0 * D2 - 2.0 * D3),
+                                         dt * (-48.0 * D2 + 12.0 * D3)], calls[1])
+        return U3 + w
+    if scheme == "exprb53":
+        y1_half, y1_nine = phi_replay(Amul, [0.5, 0.9], [None, v], calls[0])
+        D2 = _D(tm, u_n, u_n + y1_half)
+        y3_half, y3_nine = phi_replay(Amul, [0.5, 0.9], [None, None, None, dt * D2], calls[1])
+        U3 = (u_n + y1_nine + ((27.0 / 25.0) / 0.5 ** 3) * y3_half
+              + ((729.0 / 125.0) / 0.9 ** 3) * y3_nine)
+        D3 = _D(tm, u_n, U3)
+        (w,) = phi_replay(Amul, [1.0], [None, v, None, dt * (18.0 * D2 - (250.0 / 81.0) * D3),
+                                         dt * (-60.0 * D2 + (500.0 / 27.0) * D3)], calls[2])
+        return u_n + w
     raise ValueError(f"no adjoint for scheme {scheme!r}; supported: {ADJOINT_SCHEMES}")
 
 
@@ -251,7 +269,7 @@ class ReplayPhi:
 def forward_with_traces(scheme: str, swe, u0: np.ndarray, dt: float, nsteps: int,
                         opts: Optional[PhiOpts] = None):
     """Oracle forecast; returns (states u_0..u_N, per-step list of per-call traces)."""
-    ncalls = {"epi2": 1, "exprb42": 2}[scheme]
+    ncalls = NCALLS[scheme]
     phi = KrylovPhi(swe, opts or PhiOpts())
     states = [np.array(u0, dtype=np.float64)]
     traces = []

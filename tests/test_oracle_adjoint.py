@@ -27,7 +27,7 @@ def _direction(s, u, seed):
     return d
 
 
-@pytest.mark.parametrize("scheme", ["epi2", "exprb42"])
+@pytest.mark.parametrize("scheme", ["epi2", "exprb42", "pexprb43", "exprb53"])
 def test_torch_step_equals_numpy_step(scheme):
     s = oracle_swe(3)
     u0 = balanced_state(s.grid.x, 2, 400.0)
@@ -38,7 +38,8 @@ def test_torch_step_equals_numpy_step(scheme):
         assert np.linalg.norm(got - states[k + 1]) <= 1e-13 * np.linalg.norm(states[k + 1])
 
 
-@pytest.mark.parametrize("scheme,lev,nsteps", [("exprb42", 3, 2), ("epi2", 3, 2), ("exprb42", 4, 3)])
+@pytest.mark.parametrize("scheme,lev,nsteps", [("exprb42", 3, 2), ("epi2", 3, 2), ("exprb42", 4, 3),
+                                               ("pexprb43", 3, 2), ("exprb53", 3, 2)])
 def test_gradient_matches_frozen_central_difference(scheme, lev, nsteps):
     s = oracle_swe(lev)
     u0 = balanced_state(s.grid.x, 2, 400.0)
