@@ -215,7 +215,8 @@ int exprb_step(swe_grid* grid, int scheme, double dt, const double* u_n, double*
  * substep decisions of the forward step frozen (the paper defines no
  * adjoint; the derivative is the one of the computed step, Algorithm 1 with
  * the step sizes, Krylov sizes and accept/reject choices of `trace`).
- *   scheme: SWE_EPI2 or SWE_EXPRB42 (Eqs. eq3.5, eq3.11).
+ *   scheme: SWE_EPI2, SWE_EXPRB42, SWE_PEXPRB43 or SWE_EXPRB53 (Eqs. eq3.5,
+ *     eq3.11-eq3.13); epi3 (a two-step method) is not covered.
  *   u_n: the step's input state (device, n doubles), the checkpoint.
  *   trace: host array of the forward step's n_trace attempts, as exprb_step
  *     wrote them into phi_stats.trace (call indices 0..ncalls-1 in order).

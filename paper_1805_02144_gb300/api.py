@@ -279,7 +279,7 @@ class ExprbStepFunction(torch.autograd.Function):
 
 def exprb_step_differentiable(grid: Grid, scheme: str, dt: float, u_n: torch.Tensor, state: "SchemeState",
                               opts=None, trace_cap: int = 4096) -> torch.Tensor:
-    """exprb_step as a torch autograd node (EPI2 and exprb42)."""
+    """exprb_step as a torch autograd node (EPI2, exprb42, pexprb43, exprb53)."""
     return ExprbStepFunction.apply(u_n, grid, scheme, dt, state, opts, trace_cap)
 
 

@@ -29,7 +29,7 @@ struct AdjArgs {
   const double* u_lin;       // linearisation state u_n
   const double* aux;         // eta (with f) and n x u of u_lin
   double dt;
-  int p, nsub;
+  int p, nsub, ns;
   const double* ybar[NSMAX]; // adjoints of the outputs y(rho_i); nullptr = 0
   double* vbar[PMAX + 1];    // += adjoints of v_0..v_p (nullable)
   double* ubar;              // += dt sum Q'(x)^T xbar over every product A x
@@ -37,7 +37,9 @@ struct AdjArgs {
   const double* tapeW;
   const double* tapeV;
   const long long* tape_offV;
+  const long long* tape_mmax;  // largest m each substep's basis region holds
   const TapeSub* tape_sub;
+  int* status_out;           // nullable: the launch's status is stored here at exit
   // workspace
   double* Y;                 // n: adjoint of the current substep's output
   double* Wb;                // (PMAX + 1) n: adjoints of w_j

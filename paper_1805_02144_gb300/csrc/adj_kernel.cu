@@ -326,21 +326,33 @@ __device__ void adj_exp_reverse(const AdjArgs& a, AdjShared& sh, const TapeSub& 
   if (r >= 1 && r <= ADJ_TAYLOR_TERMS) sh.ck[r] = 1.0 / ((double)s * (double)r);
   if (r < M) sh.xv[r] = (r == M - 1) ? 1.0 : 0.0;
   __syncthreads();
-  // forward: x = (T_32(X/s))^s e_{M-1}, keeping the start of each step
-  for (int st = 0; st < s; ++st) {
-    double acc = r < M ? sh.xv[r] : 0.0;
-    if (r < M) xs[(size_t)st * MW + r] = acc;
-    for (int kk = 1; kk <= ADJ_TAYLOR_TERMS; ++kk) {
-      double v = r < M ? sh.ck[kk] * aug_row(sh, r, m, p, tau, sh.xv) : 0.0;
-      __syncthreads();
-      if (r < M) {
-        sh.xv[r] = v;
-        acc += v;
+  // forward: x = (T_32(X/s))^s e_{M-1}, keeping the start of each step; the
+  // terms alternate between sh.xv and sh.ob (one block barrier per term)
+  {
+    double* buf[2] = {sh.xv, sh.ob};
+    int c = 0;
+    for (int st = 0; st < s; ++st) {
+      double acc = r < M ? buf[c][r] : 0.0;
+      if (r < M) xs[(size_t)st * MW + r] = acc;
+      for (int kk = 1; kk <= ADJ_TAYLOR_TERMS; ++kk) {
+        const double v = r < M ? sh.ck[kk] * aug_row(sh, r, m, p, tau, buf[c]) : 0.0;
+        if (r < M) {
+          buf[c ^ 1][r] = v;
+          acc += v;
+        }
+        __syncthreads();
+        c ^= 1;
       }
+      if (r < M) buf[c ^ 1][r] = acc;
+      __syncthreads();
+      c ^= 1;
+    }
+    if (c != 0) {
+      const double v = r < M ? buf[c][r] : 0.0;
+      __syncthreads();
+      if (r < M) sh.xv[r] = v;
       __syncthreads();
     }
-    if (r < M) sh.xv[r] = acc;
-    __syncthreads();
   }
   // phi_{p+1}(tau H) e_1 = x[0:m]; phi_p(tau H) e_1 = tau H x + e_1 / p!
   double fact = 1.0;
@@ -393,19 +405,13 @@ __device__ void adj_exp_reverse(const AdjArgs& a, AdjShared& sh, const TapeSub& 
   __syncthreads();
   // reverse the scaling steps
   for (int st = s - 1; st >= 0; --st) {
-    // recompute this step's Taylor terms
-    if (r < M) {
-      sh.xv[r] = xs[(size_t)st * MW + r];
-      ts[r] = sh.xv[r];
-    }
+    // recompute this step's Taylor terms into ts (each term is its own row,
+    // so one block barrier per term suffices)
+    if (r < M) ts[r] = xs[(size_t)st * MW + r];
     __syncthreads();
     for (int kk = 1; kk <= ADJ_TAYLOR_TERMS; ++kk) {
-      double v = r < M ? sh.ck[kk] * aug_row(sh, r, m, p, tau, sh.xv) : 0.0;
-      __syncthreads();
-      if (r < M) {
-        sh.xv[r] = v;
-        ts[(size_t)kk * MW + r] = v;
-      }
+      const double v = r < M ? sh.ck[kk] * aug_row(sh, r, m, p, tau, ts + (size_t)(kk - 1) * MW) : 0.0;
+      if (r < M) ts[(size_t)kk * MW + r] = v;
       __syncthreads();
     }
     // out = sum_k t_k; tbar_k = obar + ck[k+1] X^T tbar_{k+1}
@@ -506,7 +512,9 @@ __device__ bool adj_run(const AdjArgs& a, AdjShared& sh) {
     const TapeSub& S = a.tape_sub[k];
     const int m = S.m;
     const bool kry = S.beta > 0.0;
-    if (kry && (S.broken || m < 1 || m > KMAX || S.s < 1 || S.s > a.xs_steps)) {
+    // the tape's scalars index buffers: check them against what the host laid out
+    if ((kry && (S.broken || m < 1 || m > KMAX || m > a.tape_mmax[k] || S.s < 1 || S.s > a.xs_steps)) ||
+        (S.land && (S.out_idx < 0 || S.out_idx >= a.ns))) {
       adj_abort(a, sh, SWE_ERR_INVALID_ARG);
       return false;
     }
@@ -701,6 +709,11 @@ __global__ void __launch_bounds__(ADJ_THREADS, ADJ_MINB) adj_kernel(AdjArgs a) {
   if (!ok && blockIdx.x == 0 && threadIdx.x == 0) {
     int ab = ld_volatile_int(&a.sync->abort);
     if (a.ctrl->status == SWE_OK) a.ctrl->status = ab != 0 ? ab : SWE_ERR_TIMEOUT;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0 && a.status_out) {
+    // other blocks may still be leaving after an abort; their statuses are the same
+    const int st = ld_volatile_int(&a.ctrl->status);
+    if (st != SWE_OK && *a.status_out == SWE_OK) *a.status_out = st;
   }
 }
 

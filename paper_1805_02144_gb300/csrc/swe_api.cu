@@ -102,7 +102,10 @@ struct swe_grid {
   AdjCtrl* actrl = nullptr;
   void* dtape = nullptr;     // tapes of the recorded forward calls (grown on demand)
   size_t tape_bytes = 0;
-  int adj_status_host = 0;
+  long long* hstage = nullptr;  // pinned staging of the tape layout (offsets, sizes)
+  size_t hstage_cap = 0;
+  cudaEvent_t stage_ev = nullptr;
+  int* adj_status = nullptr;    // device: first error of the adjoint launches of a step
 };
 
 struct swe_ensemble {
@@ -538,7 +541,7 @@ int prepare_lin(swe_grid* g, const double* u_lin, const phi_opts& o, cudaStream_
 struct TapeCall {
   double* W = nullptr;
   double* V = nullptr;
-  long long* offV = nullptr;
+  long long* offV = nullptr;  // K offsets, then K basis-slot counts (as long long)
   TapeSub* sub = nullptr;
   int K = 0;  // accepted substeps
   int p = 0;
@@ -650,7 +653,7 @@ int read_stats(swe_grid* g, phi_stats* stats, cudaStream_t st) {
 // adjoint of a step (exprb_step_adjoint)
 // ---------------------------------------------------------------------------
 constexpr int ADJ_XS_STEPS = 4096;  // scaling steps of one exponential the scratch holds
-constexpr int ADJ_VECS = 6;         // scheme-level vectors of the adjoint driver
+constexpr int ADJ_VECS = 16;        // scheme-level vectors of the adjoint driver
 
 int ensure_adjoint(swe_grid* g) {
   if (g->dadj) return SWE_OK;
@@ -668,12 +671,12 @@ int ensure_adjoint(swe_grid* g) {
                     (size_t)nb * ADJ_KW * 8,                    // partw
                     (size_t)(ADJ_XS_STEPS + 40) * mw * 8,       // xs
                     (size_t)ADJ_VECS * n * 8,                   // scheme vectors
-                    sizeof(AdjCtrl)};
+                    sizeof(AdjCtrl), sizeof(int)};
   void** dst[] = {(void**)&g->aY,   (void**)&g->aWb,    (void**)&g->aX,  (void**)&g->aP,
                   (void**)&g->aPL,  (void**)&g->aZb,    (void**)&g->apart, (void**)&g->apartw,
-                  (void**)&g->axs,  (void**)&g->avec,   (void**)&g->actrl};
+                  (void**)&g->axs,  (void**)&g->avec,   (void**)&g->actrl, (void**)&g->adj_status};
   constexpr int NP = sizeof(sizes) / sizeof(sizes[0]);
-  static_assert(NP == 11, "adjoint workspace layout");
+  static_assert(NP == 12, "adjoint workspace layout");
   size_t total = 0;
   for (size_t x : sizes) total += (x + 255) & ~size_t(255);
   cudaError_t e = cudaMalloc(&g->dadj, total);
@@ -688,6 +691,7 @@ int ensure_adjoint(swe_grid* g) {
   }
   g->adj_nblocks = nb;
   CK(cudaMemset(g->dadj, 0, total));
+  CK(cudaEventCreateWithFlags(&g->stage_ev, cudaEventDisableTiming));
   return SWE_OK;
 }
 
@@ -737,7 +741,7 @@ int plan_tape(const phi_attempt* trace, int n_trace, int ncalls, TapePlan& P) {
 int alloc_tapes(swe_grid* g, const TapePlan& P, const int* pc, int ncalls, TapeCall* out, cudaStream_t st) {
   const size_t n = (size_t)4 * g->T.ng;
   auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
-  size_t total = 0;
+  size_t total = 0, nstage = 0;
   std::vector<size_t> offW(ncalls), offV(ncalls), offO(ncalls), offS(ncalls);
   for (int c = 0; c < ncalls; ++c) {
     const size_t K = P.mmax[c].size();
@@ -748,9 +752,10 @@ int alloc_tapes(swe_grid* g, const TapePlan& P, const int* pc, int ncalls, TapeC
     offV[c] = total;
     total += al(vsz * 8);
     offO[c] = total;
-    total += al(K * sizeof(long long));
+    total += al(2 * K * sizeof(long long));
     offS[c] = total;
     total += al(K * sizeof(TapeSub));
+    nstage += 2 * K;
   }
   if (total > g->tape_bytes) {
     if (g->dtape) {
@@ -766,7 +771,17 @@ int alloc_tapes(swe_grid* g, const TapePlan& P, const int* pc, int ncalls, TapeC
     }
     g->tape_bytes = total;
   }
+  // the previous step's layout copies must have left the pinned staging
+  CK(cudaEventSynchronize(g->stage_ev));
+  if (nstage > g->hstage_cap) {
+    if (g->hstage) cudaFreeHost(g->hstage);
+    g->hstage = nullptr;
+    g->hstage_cap = 0;
+    CK(cudaMallocHost(&g->hstage, nstage * sizeof(long long)));
+    g->hstage_cap = nstage;
+  }
   char* base = (char*)g->dtape;
+  size_t pos = 0;
   for (int c = 0; c < ncalls; ++c) {
     TapeCall& t = out[c];
     t.W = (double*)(base + offW[c]);
@@ -775,15 +790,17 @@ int alloc_tapes(swe_grid* g, const TapePlan& P, const int* pc, int ncalls, TapeC
     t.sub = (TapeSub*)(base + offS[c]);
     t.K = (int)P.mmax[c].size();
     t.p = pc[c];
-    std::vector<long long> o(t.K);
+    long long* h = g->hstage + pos;
     long long acc = 0;
     for (int k = 0; k < t.K; ++k) {
-      o[k] = acc;
+      h[k] = acc;
+      h[t.K + k] = P.mmax[c][k];
       acc += (long long)(P.mmax[c][k] + 1) * (long long)n;
     }
-    CK(cudaMemcpyAsync(t.offV, o.data(), o.size() * sizeof(long long), cudaMemcpyHostToDevice, st));
-    CK(cudaStreamSynchronize(st));  // o is released on return
+    CK(cudaMemcpyAsync(t.offV, h, 2 * (size_t)t.K * sizeof(long long), cudaMemcpyHostToDevice, st));
+    pos += 2 * (size_t)t.K;
   }
+  CK(cudaEventRecord(g->stage_ev, st));
   return SWE_OK;
 }
 
@@ -805,7 +822,10 @@ int adj_call(swe_grid* g, const TapeCall& tp, const double* u_lin, double dt, co
   a.tapeW = tp.W;
   a.tapeV = tp.V;
   a.tape_offV = tp.offV;
+  a.tape_mmax = tp.offV + tp.K;
   a.tape_sub = tp.sub;
+  a.ns = ns;
+  a.status_out = g->adj_status;
   a.Y = g->aY;
   a.Wb = g->aWb;
   a.X = g->aX;
@@ -822,9 +842,6 @@ int adj_call(swe_grid* g, const TapeCall& tp, const double* u_lin, double dt, co
   int e = launch_adj_kernel(a, g->adj_nblocks, st);
   if (e != 0) return cuda_fail((cudaError_t)e, "cudaLaunchCooperativeKernel(adj_kernel)");
   count_launches(g, 1);
-  CK(cudaMemcpyAsync(&g->adj_status_host, &g->actrl->status, sizeof(int), cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
-  if (g->adj_status_host != SWE_OK) return fail(g->adj_status_host, "adj_kernel reported an error");
   return SWE_OK;
 }
 
@@ -962,6 +979,8 @@ void swe_destroy_grid(swe_grid* g) {
   if (g->replay) cudaFree(g->replay);
   if (g->dadj) cudaFree(g->dadj);
   if (g->dtape) cudaFree(g->dtape);
+  if (g->hstage) cudaFreeHost(g->hstage);
+  if (g->stage_ev) cudaEventDestroy(g->stage_ev);
   delete g;
 }
 
@@ -1222,8 +1241,8 @@ int exprb_step_adjoint(swe_grid* g, int scheme, double dt, const double* u_n, co
   if (!g || !u_n || !trace || !lam_np1 || !lam_n)
     return fail(SWE_ERR_INVALID_ARG, "exprb_step_adjoint: NULL argument");
   if (lam_n == lam_np1 || lam_n == u_n) return fail(SWE_ERR_INVALID_ARG, "exprb_step_adjoint: lam_n must not alias");
-  if (scheme != SWE_EPI2 && scheme != SWE_EXPRB42)
-    return fail(SWE_ERR_INVALID_ARG, "exprb_step_adjoint: EPI2 and exprb42 are supported");
+  if (scheme != SWE_EPI2 && scheme != SWE_EXPRB42 && scheme != SWE_PEXPRB43 && scheme != SWE_EXPRB53)
+    return fail(SWE_ERR_INVALID_ARG, "exprb_step_adjoint: EPI2, exprb42, pexprb43 and exprb53 are supported");
   if (n_trace < 1) return fail(SWE_ERR_INVALID_ARG, "exprb_step_adjoint: empty trace");
   int rc;
   phi_opts o;
@@ -1232,81 +1251,185 @@ int exprb_step_adjoint(swe_grid* g, int scheme, double dt, const double* u_n, co
   if ((rc = ensure_workspace(g))) return rc;
   if ((rc = ensure_adjoint(g))) return rc;
   cudaStream_t st = S(stream);
-  const int ncalls = scheme == SWE_EPI2 ? 1 : 2;
-  const int pc[2] = {1, 3};
+  // the scheme's phi calls: p of each call
+  int ncalls = 1;
+  int pc[3] = {1, 0, 0};
+  if (scheme == SWE_EXPRB42) {
+    ncalls = 2;
+    pc[1] = 3;
+  } else if (scheme == SWE_PEXPRB43) {
+    ncalls = 2;
+    pc[1] = 4;
+  } else if (scheme == SWE_EXPRB53) {
+    ncalls = 3;
+    pc[1] = 3;
+    pc[2] = 4;
+  }
   TapePlan P;
   if ((rc = plan_tape(trace, n_trace, ncalls, P))) return rc;
-  TapeCall tapes[2];
+  TapeCall tapes[3];
   if ((rc = alloc_tapes(g, P, pc, ncalls, tapes, st))) return rc;
   // forward replay with tapes: the same calls as exprb_step
   o.replay = P.replay.data();
   o.n_replay = (int)(P.replay.size() / 3);
   if ((rc = stage_replay(g, o, st))) return rc;
   const size_t n = (size_t)4 * g->T.ng;
-  double* vF = g->avec;
-  double* Y1 = g->avec + n;
-  double* v3 = g->avec + 2 * n;
-  double* yw = g->avec + 3 * n;    // forward output (not needed)
-  double* VB1 = g->avec + 4 * n;   // adjoint of v_1 = dt F(u_n)
-  double* VB3 = g->avec + 5 * n;   // adjoint of v_3 (exprb42), then of Y1
+  double* B[ADJ_VECS];
+  for (int k = 0; k < ADJ_VECS; ++k) B[k] = g->avec + (size_t)k * n;
+  double* vF = B[0];  // dt F(u_n)
+  double* yw = B[1];  // forward output of the last call (not needed)
   ProfSpan span(g, st, &g->call_ev);
   CK(cudaMemsetAsync(g->stats, 0, sizeof(DevStats), st));
+  CK(cudaMemsetAsync(g->adj_status, 0, sizeof(int), st));
   if ((rc = prepare_lin(g, u_n, o, st))) return rc;
   if ((rc = run_rhs(g, u_n, vF, dt, st))) return rc;
-  const double one = 1.0, r1 = 0.75;
+  const double one = 1.0;
+  auto call = [&](int c, int p, const double* const* v, int ns, const double* rho, double* const* y) {
+    return phi_call(g, u_n, dt, p, v, ns, rho, y, o, c, nullptr, P.first[c], st, &tapes[c]);
+  };
+  // exprb53 stage weights of U_3 (Eq. eq3.13 with the rho^3 of Y_3)
+  const double c3h = (27.0 / 25.0) / (0.5 * 0.5 * 0.5);
+  const double c3n = (729.0 / 125.0) / (0.9 * 0.9 * 0.9);
   if (scheme == SWE_EPI2) {
     const double* v[2] = {nullptr, vF};
     double* y[1] = {yw};
-    if ((rc = phi_call(g, u_n, dt, 1, v, 1, &one, y, o, 0, nullptr, P.first[0], st, &tapes[0]))) return rc;
-  } else {
+    if ((rc = call(0, 1, v, 1, &one, y))) return rc;
+  } else if (scheme == SWE_EXPRB42) {
+    const double r1 = 0.75;
     const double* v1[2] = {nullptr, vF};
-    double* y1[1] = {Y1};
-    if ((rc = phi_call(g, u_n, dt, 1, v1, 1, &r1, y1, o, 0, nullptr, P.first[0], st, &tapes[0]))) return rc;
-    if ((rc = run_quad(g, Y1, v3, (32.0 / 9.0) * dt, st))) return rc;
-    const double* v2[4] = {nullptr, vF, nullptr, v3};
+    double* y1[1] = {B[2]};                                          // Y1
+    if ((rc = call(0, 1, v1, 1, &r1, y1))) return rc;
+    if ((rc = run_quad(g, B[2], B[3], (32.0 / 9.0) * dt, st))) return rc;  // v_3
+    const double* v2[4] = {nullptr, vF, nullptr, B[3]};
     double* y2[1] = {yw};
-    if ((rc = phi_call(g, u_n, dt, 3, v2, 1, &one, y2, o, 1, nullptr, P.first[1], st, &tapes[1]))) return rc;
+    if ((rc = call(1, 3, v2, 1, &one, y2))) return rc;
+  } else if (scheme == SWE_PEXPRB43) {
+    const double r1[2] = {0.5, 1.0};
+    const double* v1[2] = {nullptr, vF};
+    double* y1[2] = {B[2], B[3]};                                    // Y(1/2), Y(1)
+    if ((rc = call(0, 1, v1, 2, r1, y1))) return rc;
+    if ((rc = run_quad(g, B[2], B[4], dt, st))) return rc;           // dt D_2
+    if ((rc = run_quad(g, B[3], B[5], dt, st))) return rc;           // dt D_3
+    if ((rc = run_lincomb(g, B[6], {{16.0, B[4]}, {-2.0, B[5]}}, st))) return rc;
+    if ((rc = run_lincomb(g, B[7], {{-48.0, B[4]}, {12.0, B[5]}}, st))) return rc;
+    const double* v2[5] = {nullptr, nullptr, nullptr, B[6], B[7]};
+    double* y2[1] = {yw};
+    if ((rc = call(1, 4, v2, 1, &one, y2))) return rc;
+  } else {  // SWE_EXPRB53
+    const double r1[2] = {0.5, 0.9};
+    const double* v1[2] = {nullptr, vF};
+    double* y1[2] = {B[2], B[3]};                                    // Y_1(1/2), Y_1(9/10)
+    if ((rc = call(0, 1, v1, 2, r1, y1))) return rc;
+    if ((rc = run_quad(g, B[2], B[4], dt, st))) return rc;           // dt D_2
+    const double* v2[4] = {nullptr, nullptr, nullptr, B[4]};
+    double* y2[2] = {B[5], B[6]};                                    // Y_3(1/2), Y_3(9/10)
+    if ((rc = call(1, 3, v2, 2, r1, y2))) return rc;
+    if ((rc = run_lincomb(g, B[7], {{1.0, B[3]}, {c3h, B[5]}, {c3n, B[6]}}, st))) return rc;  // U_3 - u_n
+    if ((rc = run_quad(g, B[7], B[8], dt, st))) return rc;           // dt D_3
+    if ((rc = run_lincomb(g, B[9], {{18.0, B[4]}, {-250.0 / 81.0, B[8]}}, st))) return rc;
+    if ((rc = run_lincomb(g, B[10], {{-60.0, B[4]}, {500.0 / 27.0, B[8]}}, st))) return rc;
+    const double* v3[5] = {nullptr, vF, nullptr, B[9], B[10]};
+    double* y3[1] = {yw};
+    if ((rc = call(2, 4, v3, 1, &one, y3))) return rc;
   }
-  {
-    DevStats ds;
-    CK(cudaMemcpyAsync(&ds, g->stats, sizeof(DevStats), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    if (ds.status != SWE_OK) return fail(ds.status, "exprb_step_adjoint: forward replay failed");
-    if (stats) {
-      stats->n_jv = ds.n_jv;
-      stats->n_substeps = ds.n_sub;
-      stats->n_reject = ds.n_rej;
-      stats->m_last = ds.m_last;
-      stats->m_max_used = ds.m_max_used;
-      stats->status = ds.status;
-      stats->n_trace = 0;
-    }
-  }
-  // reverse: u_{n+1} = u_n + y
-  CK(cudaMemcpyAsync(lam_n, lam_np1, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  // reverse (the tape's scalars are checked by the reverse launch against the
+  // layout, so a failed recomputation cannot send it out of bounds; its
+  // status is read once at the end).  Adjoint vectors: VB1 of v_1 = dt F(u_n); the rest per scheme.
+  double* VB1 = B[11];
+  double* T1 = B[12];
+  double* T2 = B[13];
+  double* T3 = B[14];
+  double* T4 = B[15];
+  double* auxq = B[1];  // aux planes for Q'^T (yw is not needed any more)
+  CK(cudaMemcpyAsync(lam_n, lam_np1, n * sizeof(double), cudaMemcpyDeviceToDevice, st));  // u_{n+1} = u_n + ...
   CK(cudaMemsetAsync(VB1, 0, n * sizeof(double), st));
+  auto zero = [&](double* x) { return cudaMemsetAsync(x, 0, n * sizeof(double), st); };
   if (scheme == SWE_EPI2) {
     const double* yb[1] = {lam_np1};
     double* vb[2] = {nullptr, VB1};
     if ((rc = adj_call(g, tapes[0], u_n, dt, yb, 1, vb, lam_n, st))) return rc;
-  } else {
-    CK(cudaMemsetAsync(VB3, 0, n * sizeof(double), st));
+  } else if (scheme == SWE_EXPRB42) {
+    CK(zero(T1));
     {
       const double* yb[1] = {lam_np1};
-      double* vb[4] = {nullptr, VB1, nullptr, VB3};
+      double* vb[4] = {nullptr, VB1, nullptr, T1};                   // T1: adjoint of v_3
       if ((rc = adj_call(g, tapes[1], u_n, dt, yb, 1, vb, lam_n, st))) return rc;
     }
-    // v_3 = (32/9) dt Q(Y1): Ybar1 = (32/9) dt Q'(Y1)^T VB3 (into yw)
-    if ((rc = run_transposed<MODE_QT>(g, Y1, VB3, (32.0 / 9.0) * dt, 0, yw, v3, st))) return rc;
+    // v_3 = (32/9) dt Q(Y1): adjoint of Y1 into T2
+    if ((rc = run_transposed<MODE_QT>(g, B[2], T1, (32.0 / 9.0) * dt, 0, T2, auxq, st))) return rc;
     {
-      const double* yb[1] = {yw};
+      const double* yb[1] = {T2};
       double* vb[2] = {nullptr, VB1};
       if ((rc = adj_call(g, tapes[0], u_n, dt, yb, 1, vb, lam_n, st))) return rc;
+    }
+  } else if (scheme == SWE_PEXPRB43) {
+    CK(zero(T1));
+    CK(zero(T2));
+    {
+      const double* yb[1] = {lam_np1};
+      double* vb[5] = {nullptr, nullptr, nullptr, T1, T2};           // adjoints of v_3, v_4
+      if ((rc = adj_call(g, tapes[1], u_n, dt, yb, 1, vb, lam_n, st))) return rc;
+    }
+    // v_3 = 16 dD_2 - 2 dD_3, v_4 = -48 dD_2 + 12 dD_3 (dD = dt D):
+    // adjoints of dt D_2 (T3) and dt D_3 (T4)
+    if ((rc = run_lincomb(g, T3, {{16.0, T1}, {-48.0, T2}}, st))) return rc;
+    if ((rc = run_lincomb(g, T4, {{-2.0, T1}, {12.0, T2}}, st))) return rc;
+    // dt D_2 = dt Q(Y(1/2)), dt D_3 = dt Q(Y(1)); u_{n+1} = u_n + Y(1) + w
+    if ((rc = run_transposed<MODE_QT>(g, B[2], T3, dt, 0, T1, auxq, st))) return rc;       // Ybar(1/2)
+    CK(cudaMemcpyAsync(T2, lam_np1, n * sizeof(double), cudaMemcpyDeviceToDevice, st));   // Ybar(1)
+    if ((rc = run_transposed<MODE_QT>(g, B[3], T4, dt, 1, T2, auxq, st))) return rc;
+    {
+      const double* yb[2] = {T1, T2};
+      double* vb[2] = {nullptr, VB1};
+      if ((rc = adj_call(g, tapes[0], u_n, dt, yb, 2, vb, lam_n, st))) return rc;
+    }
+  } else {  // SWE_EXPRB53
+    CK(zero(T1));
+    CK(zero(T2));
+    {
+      const double* yb[1] = {lam_np1};
+      double* vb[5] = {nullptr, VB1, nullptr, T1, T2};               // adjoints of v_1, v_3, v_4
+      if ((rc = adj_call(g, tapes[2], u_n, dt, yb, 1, vb, lam_n, st))) return rc;
+    }
+    // v_3 = 18 dD_2 - 250/81 dD_3, v_4 = -60 dD_2 + 500/27 dD_3
+    if ((rc = run_lincomb(g, T3, {{18.0, T1}, {-60.0, T2}}, st))) return rc;                // of dt D_2
+    if ((rc = run_lincomb(g, T4, {{-250.0 / 81.0, T1}, {500.0 / 27.0, T2}}, st))) return rc;  // of dt D_3
+    // dt D_3 = dt Q(U_3 - u_n), U_3 - u_n = Y_1(9/10) + c3h Y_3(1/2) + c3n Y_3(9/10)
+    if ((rc = run_transposed<MODE_QT>(g, B[7], T4, dt, 0, T1, auxq, st))) return rc;       // of U_3 - u_n
+    if ((rc = run_lincomb(g, T2, {{c3h, T1}}, st))) return rc;                              // of Y_3(1/2)
+    if ((rc = run_lincomb(g, T4, {{c3n, T1}}, st))) return rc;                              // of Y_3(9/10)
+    {
+      const double* yb[2] = {T2, T4};
+      double* vb[4] = {nullptr, nullptr, nullptr, T3};               // += adjoint of dt D_2
+      if ((rc = adj_call(g, tapes[1], u_n, dt, yb, 2, vb, lam_n, st))) return rc;
+    }
+    // dt D_2 = dt Q(Y_1(1/2)); Y_1(9/10) has the adjoint of U_3 - u_n (T1)
+    if ((rc = run_transposed<MODE_QT>(g, B[2], T3, dt, 0, T2, auxq, st))) return rc;       // of Y_1(1/2)
+    {
+      const double* yb[2] = {T2, T1};
+      double* vb[2] = {nullptr, VB1};
+      if ((rc = adj_call(g, tapes[0], u_n, dt, yb, 2, vb, lam_n, st))) return rc;
     }
   }
   // v_1 = dt F(u_n): lam_n += dt J(u_n)^T VB1
   if ((rc = run_transposed<MODE_JT>(g, u_n, VB1, dt, 1, lam_n, nullptr, st))) return rc;
   span.finish();
+  DevStats ds;
+  int ast = SWE_OK;
+  CK(cudaMemcpyAsync(&ds, g->stats, sizeof(DevStats), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&ast, g->adj_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (stats) {
+    stats->n_jv = ds.n_jv;
+    stats->n_substeps = ds.n_sub;
+    stats->n_reject = ds.n_rej;
+    stats->m_last = ds.m_last;
+    stats->m_max_used = ds.m_max_used;
+    stats->status = ds.status != SWE_OK ? ds.status : ast;
+    stats->n_trace = 0;
+  }
+  if (ds.status != SWE_OK) return fail(ds.status, "exprb_step_adjoint: the forward recomputation failed");
+  if (ast != SWE_OK) return fail(ast, "exprb_step_adjoint: the reverse launch reported an error");
   return SWE_OK;
 }
 

@@ -118,7 +118,8 @@ def _replay(trace):
     return [[r["tau"], r["m"], 1.0 if r["accepted"] else 0.0] for r in trace]
 
 
-@pytest.mark.parametrize("scheme,lev", [("epi2", 3), ("exprb42", 3), ("exprb42", 5)])
+@pytest.mark.parametrize("scheme,lev", [("epi2", 3), ("exprb42", 3), ("exprb42", 5), ("pexprb43", 3),
+                                        ("pexprb43", 5), ("exprb53", 3), ("exprb53", 5)])
 def test_step_adjoint_matches_oracle(scheme, lev):
     from oracle.adjoint import TorchSWE, forward_with_traces, step_vjp
     from paper_1805_02144_gb300.api import exprb_step_adjoint
@@ -139,7 +140,8 @@ def test_step_adjoint_matches_oracle(scheme, lev):
         assert err <= 1e-9, err
 
 
-def test_step_adjoint_matches_gpu_frozen_central_difference():
+@pytest.mark.parametrize("scheme", ["exprb42", "pexprb43", "exprb53"])
+def test_step_adjoint_matches_gpu_frozen_central_difference(scheme):
     """<lam, dS/du d> by a central difference of the GPU step replaying the
     forward's decisions, against <S'^T lam, d> from the adjoint."""
     from paper_1805_02144_gb300.api import SchemeState, exprb_step, exprb_step_adjoint, Grid
@@ -147,7 +149,7 @@ def test_step_adjoint_matches_gpu_frozen_central_difference():
     x = G.cell_centres()
     u0 = balanced_state(x, 3, 400.0)
     dt = 1800.0
-    states, traces = _gpu_forward(G, "exprb42", u0, dt, 2)
+    states, traces = _gpu_forward(G, scheme, u0, dt, 2)
     ng = G.ncells
     for k in range(2):
         lam = random_vector(G.n, 70 + k)
@@ -155,11 +157,11 @@ def test_step_adjoint_matches_gpu_frozen_central_difference():
         un = host(states[k])
         d[:3 * ng] *= np.abs(un[:3 * ng]).max()
         d[3 * ng:] *= 400.0
-        adj = host(exprb_step_adjoint(G, "exprb42", dt, states[k], traces[k], dev(lam)))
+        adj = host(exprb_step_adjoint(G, scheme, dt, states[k], traces[k], dev(lam)))
         eps = 1e-6
         rp = {"replay": _replay(traces[k])}
-        up = host(exprb_step(G, "exprb42", dt, dev(un + eps * d), state=SchemeState(G), opts=rp))
-        um = host(exprb_step(G, "exprb42", dt, dev(un - eps * d), state=SchemeState(G), opts=rp))
+        up = host(exprb_step(G, scheme, dt, dev(un + eps * d), state=SchemeState(G), opts=rp))
+        um = host(exprb_step(G, scheme, dt, dev(un - eps * d), state=SchemeState(G), opts=rp))
         fd = lam @ (up - um) / (2 * eps)
         assert abs(fd - adj @ d) <= 1e-7 * abs(fd), (fd, adj @ d)
 
@@ -255,3 +257,5 @@ def test_adjoint_rejects_mismatched_traces():
     bad = [dict(r) for r in traces[0] if r["call"] == 0]
     with pytest.raises(RuntimeError):      # second call missing
         exprb_step_adjoint(G, "exprb42", 900.0, u, bad, lam)
+    with pytest.raises(RuntimeError):      # epi3 needs the adjoint of its history term
+        exprb_step_adjoint(G, "epi3", 900.0, u, traces[0], lam)
