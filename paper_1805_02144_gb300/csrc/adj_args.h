@@ -47,7 +47,7 @@ struct AdjArgs {
   double* P;                 // 2 n: partial basis adjoints (ring)
   double* PL;                // 10 ng: transposed pass-1 planes
   double* Zb;                // n: the vector being transposed
-  double* part;              // nblocks x NRED
+  double* part;              // NRED x nblocks (value-major)
   double* partw;             // nblocks x ADJ_KW
   double* xs;                // (xs_steps + TAYLOR + 1) x (KMAX + PMAX + 2)
   int xs_steps;

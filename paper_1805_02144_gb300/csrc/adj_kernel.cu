@@ -59,8 +59,7 @@ struct AdjShared {
   int gb, gn;
   unsigned long long t_last;
   double red[(ADJ_THREADS / 32) * NRED];
-  int last, ok;
-  unsigned int gen;
+  int ok;
   ColCoef cc;
   double ck[ADJ_TAYLOR_TERMS + 2];
   double tb[MW + 2], ob[MW + 2], xv[MW + 2];
@@ -212,8 +211,8 @@ __device__ __forceinline__ void adj_abort(const AdjArgs& a, SH& sh, int code) {
 // Wide grid reduction: nv dot products <vecs_r, Y> over all cells (vecs_r for
 // r < nv0: raw basis slots of substep k; r = nv0, nv0+1: <r_m, r_{m-2}>,
 // <r_m, r_{m-1}>), summed per block in a fixed order, then over blocks in
-// block order by the last block to arrive, which runs `last(tot)` with all its
-// threads before releasing the barrier.
+// block order by block 0, which runs `last()` with all its threads between
+// two grid barriers.
 template <class LastFn>
 __device__ bool adj_wide_reduce(const AdjArgs& a, AdjShared& sh, const CellLoop& CL, int k, const TapeSub& S,
                                 int m, LastFn last) {
@@ -242,35 +241,20 @@ __device__ bool adj_wide_reduce(const AdjArgs& a, AdjShared& sh, const CellLoop&
     block_sum<1>(v1, sh.red);
     if (threadIdx.x == 0) a.partw[(size_t)sh.gb * ADJ_KW + r] = v1[0];
   }
-  if (threadIdx.x == 0) {
-    bool l;
-    sh.gen = bar_arrive(a.sync, sh.gn, &l);
-    sh.last = l;
-  }
-  __syncthreads();
-  if (sh.last) {
-    __threadfence();
+  // all block totals published; block 0 sums them in block order and runs
+  // `last` with all its threads while the others wait at the second barrier
+  if (!grid_barrier(a, sh, AP_A)) return false;
+  if (sh.gb == 0) {
     for (int r = threadIdx.x; r < nv; r += blockDim.x) {
       double s = 0.0;
-      for (int b = 0; b < sh.gn; ++b) s += ((volatile double*)a.partw)[(size_t)b * ADJ_KW + r];
+      for (int b = 0; b < sh.gn; ++b) s += __ldcg(a.partw + (size_t)b * ADJ_KW + r);
       a.ctrl->wide[r] = s;
     }
-    __threadfence_block();
     __syncthreads();
     last();
-    __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) {
-      bar_release(a.sync, sh.gen);
-      sh.ok = ld_volatile_int(&a.sync->abort) == 0;
-    }
-  } else if (threadIdx.x == 0) {
-    bool ok = bar_wait(a.sync, sh.gen, SWE_ERR_TIMEOUT);
-    sh.ok = ok && (ld_volatile_int(&a.sync->abort) == 0);
   }
-  if (threadIdx.x == 0) phase_tick(a, sh, AP_A);
-  __syncthreads();
-  return sh.ok;
+  return grid_barrier(a, sh, AP_A);
 }
 
 // Row r < m of tau H times v (the forward's operation order).
@@ -616,7 +600,7 @@ __device__ bool adj_run(const AdjArgs& a, AdjShared& sh) {
           }
         }
         const TapeSub* Sp = &S;
-        auto post = [Sp, j](volatile AdjCtrl* c) {
+        auto post = [Sp, j](volatile AdjCtrl* c, bool) {
           volatile AdjCtrl* cc2 = c;
           const TapeSub& St = *Sp;
           if (j >= 1) {

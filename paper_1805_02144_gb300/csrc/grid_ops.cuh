@@ -1,8 +1,9 @@
 // Persistent-kernel building blocks shared by the phipm_simul_iom2 launch and
 // its adjoint: per-block cell ranges, fixed-order block sums, bounded grid
-// barriers and grid reductions.  A (launch arguments) provides part, ctrl,
-// sync and prof; SH (the kernel's shared-memory struct) provides gb, gn,
-// t_last, red, gen, last and ok; ctrl's type provides red[].
+// barriers and grid reductions.  A (launch arguments) provides part (at
+// least NRED x gn doubles), ctrl, sync and prof; SH (the kernel's
+// shared-memory struct) provides gb, gn, t_last, red and ok; ctrl's type
+// provides red[].
 #pragma once
 #include <cuda_runtime.h>
 
@@ -72,54 +73,65 @@ template <class A, class SH>
 __device__ bool grid_barrier(const A& a, SH& sh, int phase) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    bool last;
-    unsigned int gen = bar_arrive(a.sync, sh.gn, &last);
-    bool ok = true;
-    if (last)
-      bar_release(a.sync, gen);
-    else
-      ok = bar_wait(a.sync, gen, SWE_ERR_TIMEOUT);
-    sh.ok = ok && (ld_volatile_int(&a.sync->abort) == 0);
+    sh.ok = flip_barrier(a.sync, sh.gb, sh.gn, SWE_ERR_TIMEOUT);
     phase_tick(a, sh, phase);
   }
   __syncthreads();
   return sh.ok;
 }
 
-// Grid reduction of K per-thread partials, then a barrier.  The last block
-// to arrive sums the block partials in block order, stores them in
-// ctrl->red[], runs post(ctrl) on its thread 0, and releases the barrier.
+// Grid reduction of K per-thread partials, then a barrier.  Each block sums
+// its threads in a fixed order and publishes its totals (value k of block b
+// at part[k * gn + b]); warp 0 of the block that arrives last sums them over
+// blocks (lane l takes blocks l, l+32, ..., then a fixed shuffle tree, so the
+// result is bitwise reproducible), stores them in ctrl->red[], runs
+// post(ctrl, true) on its lane 0 and publishes; the other blocks wait for
+// the publication.
 template <int K, class A, class SH, class Post>
 __device__ bool grid_reduce(const A& a, SH& sh, double (&v)[K], int phase, Post post) {
+  static_assert(K <= NRED, "reduction width");
   block_sum<K>(v, sh.red);
-  if (threadIdx.x == 0) {
-    for (int k = 0; k < K; ++k) a.part[(size_t)sh.gb * NRED + k] = v[k];
-    bool last;
-    sh.gen = bar_arrive(a.sync, sh.gn, &last);
-    sh.last = last;
-  }
-  __syncthreads();
-  if (sh.last) {
-    double tot[K];
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      double s = 0.0;
-      for (int b = threadIdx.x; b < sh.gn; b += blockDim.x) s += a.part[(size_t)b * NRED + k];
-      tot[k] = s;
-    }
-    block_sum<K>(tot, sh.red);
+  if (threadIdx.x < 32) {
+    GridSync* s = a.sync;
+    const int gn = sh.gn;
+    unsigned int lastu = 0, g0 = 0;
     if (threadIdx.x == 0) {
-      auto* vc = make_volatile(a.ctrl);
-      for (int k = 0; k < K; ++k) vc->red[k] = tot[k];
-      post(vc);
-      bar_release(a.sync, sh.gen);
-      sh.ok = ld_volatile_int(&a.sync->abort) == 0;
+      for (int k = 0; k < K; ++k) a.part[(size_t)k * gn + sh.gb] = v[k];
+      g0 = *(volatile unsigned int*)&s->rgen;  // cannot advance before this block arrives
+      bool last;
+      flip_arrive(s, sh.gb, gn, &last);
+      lastu = last ? 1u : 0u;
     }
-  } else if (threadIdx.x == 0) {
-    bool ok = bar_wait(a.sync, sh.gen, SWE_ERR_TIMEOUT);
-    sh.ok = ok && (ld_volatile_int(&a.sync->abort) == 0);
+    lastu = __shfl_sync(0xffffffffu, lastu, 0);
+    g0 = __shfl_sync(0xffffffffu, g0, 0);
+    if (lastu) {
+      __threadfence();
+      double t[K];
+#pragma unroll
+      for (int k = 0; k < K; ++k) t[k] = 0.0;
+      for (int b = threadIdx.x; b < gn; b += 32)
+#pragma unroll
+        for (int k = 0; k < K; ++k) t[k] += __ldcg(a.part + (size_t)k * gn + b);
+#pragma unroll
+      for (int k = 0; k < K; ++k)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t[k] += __shfl_down_sync(0xffffffffu, t[k], o);
+      if (threadIdx.x == 0) {
+        auto* vc = make_volatile(a.ctrl);
+        for (int k = 0; k < K; ++k) vc->red[k] = t[k];
+        post(vc, true);
+        __threadfence();
+        *(volatile unsigned int*)&s->rgen = g0 + 1;
+        sh.ok = ld_volatile_int(&s->abort) == 0;
+      }
+    } else if (threadIdx.x == 0) {
+      const volatile unsigned int* rg = &s->rgen;
+      const bool ok = bounded_spin(s, SWE_ERR_TIMEOUT, [&] { return *rg == g0; });
+      __threadfence();
+      sh.ok = ok && ld_volatile_int(&s->abort) == 0;
+    }
+    if (threadIdx.x == 0) phase_tick(a, sh, phase);
   }
-  if (threadIdx.x == 0) phase_tick(a, sh, phase);
   __syncthreads();
   return sh.ok;
 }

@@ -84,7 +84,7 @@ struct PhiArgsT {
   R* tmp;                   // 8 x ng pass-1 planes (Laplacian 4, scalar/vector 4)
   R* Lring;                 // 3 x n: Laplacian planes of the last three raw slots
   R* Zbuf;                  // n: A v_j before orthogonalisation
-  double* part;             // nblocks x NRED partial sums
+  double* part;             // NRED x nblocks partial sums (value-major)
   PhiCtrl* ctrl;
   GridSync* sync;
   DevStats* stats;          // accumulated (not reset by the kernel)

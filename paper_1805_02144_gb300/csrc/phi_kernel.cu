@@ -40,9 +40,7 @@ struct Shared {
   double red[(PHI_MAX_THREADS / 32) * NRED];
   double coef[KMAX + PMAX + 4];
   float coeff[KMAX + PMAX + 4];
-  int last;
   int ok;
-  unsigned int gen;
   // decision scratch (block 0, warp 0)
   double x[KMAX + PMAX + 8], y[KMAX + PMAX + 8];
   double ck[40];
@@ -428,7 +426,7 @@ __device__ bool phi_run(const PhiArgsT<R>& a, Shared& sh) {
     const int pp = p, tol_mode = a.tol_mode, m_max = a.m_max;
     const double rho0 = a.rho[0];
     const int m_init = (a.m_slot && *a.m_slot > 0) ? *a.m_slot : a.m_init;
-    auto post = [pp, tol_mode, m_max, rho0, m_init](volatile PhiCtrl* c) {
+    auto post = [pp, tol_mode, m_max, rho0, m_init](volatile PhiCtrl* c, bool) {
       double mx = 0.0;
       for (int l = 0; l <= pp; ++l) mx = fmax(mx, (double)c->red[1 + l]);
       double scale = tol_mode == 0 ? sqrt(mx) : 1.0;
@@ -509,9 +507,9 @@ __device__ bool phi_run(const PhiArgsT<R>& a, Shared& sh) {
         }
         double v[2] = {(double)nzc, (double)sqs};
         GridSync* gs = a.sync;
-        auto post = [gs, j, nz_prev, p](volatile PhiCtrl* c) {
+        auto post = [gs, j, nz_prev, p](volatile PhiCtrl* c, bool leader) {
           c->wnz[j] = c->red[0] > 0.0;
-          if (nz_prev) {
+          if (nz_prev && leader) {
             c->n_jv += 1;
             c->n_wjv += 1;
           }
@@ -577,7 +575,7 @@ __device__ bool phi_run(const PhiArgsT<R>& a, Shared& sh) {
               }
             }
             double v[2] = {(double)d0, (double)d1};
-            auto post_dots = [j](volatile PhiCtrl* c) {
+            auto post_dots = [j](volatile PhiCtrl* c, bool) {
               if (j > 0) c->hu[j - 1] = c->sig[j - 1] * c->red[0];
               c->hd[j] = c->sig[j] * c->red[1];
             };
@@ -590,12 +588,14 @@ __device__ bool phi_run(const PhiArgsT<R>& a, Shared& sh) {
               nrm += orth_pass1_cell(T, i, a.Zbuf, rj, rjm, aj, am, Lj, Ljm, rj1, Lj1, a.u_lin, SQ);
             double w[1] = {(double)nrm};
             GridSync* gs = a.sync;
-            auto post_norm = [gs, j, bd](volatile PhiCtrl* c) {
+            auto post_norm = [gs, j, bd](volatile PhiCtrl* c, bool leader) {
               double hn = sqrt((double)c->red[0]);
               double ref = fabs((double)c->hd[j]) + (j > 0 ? fabs((double)c->hu[j - 1]) : 0.0);
               c->size = j + 1;
-              c->n_jv += 1;
-              c->n_iter += 1;
+              if (leader) {
+                c->n_jv += 1;
+                c->n_iter += 1;
+              }
               if (!isfinite(hn) || !isfinite(ref)) {
                 c->status = SWE_ERR_NONFINITE;
                 atomicCAS(&gs->abort, 0, SWE_ERR_NONFINITE);
@@ -645,7 +645,7 @@ __device__ bool phi_run(const PhiArgsT<R>& a, Shared& sh) {
           }
         }
         double v[1] = {(double)nzy};
-        auto post_y = [](volatile PhiCtrl* c) { c->wnz[0] = c->red[0] > 0.0; };
+        auto post_y = [](volatile PhiCtrl* c, bool) { c->wnz[0] = c->red[0] > 0.0; };
         if (!grid_reduce<1>(a, sh, v, PH_COMBINE, post_y)) return false;
         break;
       }

@@ -372,14 +372,20 @@ __device__ __forceinline__ void pass2T_cell(const Tables& T, int j, const double
 
 // ---------------------------------------------------------------------------
 // Bounded grid-wide barrier for co-resident (cooperatively launched) blocks.
-// Every wait gives up after kWaitNs of global time, records SWE timeout in
-// *abort and returns false; a set abort word also ends every wait.
+// One arrival counter per barrier object: every block adds 1 except block 0,
+// which adds 2^31 - (n - 1), so the n-th arrival flips bit 31 whatever the
+// order and the low bits return to their value; a block waits for bit 31 to
+// differ from what its own arrival saw (no separate release store).  Every
+// wait gives up after kWaitNs of global time, records the timeout in *abort
+// and returns false; a set abort word also ends every wait.
 // ---------------------------------------------------------------------------
 struct GridSync {
-  unsigned int count;
-  unsigned int gen;
-  int abort;     // 0, or the SWE_ERR_* code that ended the launch
-  int pad;
+  unsigned int count;  // arrival counter (bit 31 flips once per barrier)
+  int pad0[31];        // count alone on its 128-byte line
+  unsigned int rgen;   // results published by grid reductions (incremented per reduction)
+  int pad1[31];
+  int abort;           // 0, or the SWE_ERR_* code that ended the launch
+  int pad2[31];
 };
 
 constexpr unsigned long long kWaitNs = 4000000000ull;  // 4 s
@@ -389,43 +395,53 @@ __device__ __forceinline__ unsigned long long globaltimer() {
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
-__device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p) {
-  unsigned int v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void st_release(unsigned int* p, unsigned int v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
 __device__ __forceinline__ int ld_volatile_int(const int* p) { return *(volatile const int*)p; }
 
-// Phase 1 of a barrier: arrive.  Returns the generation to wait on and
-// whether this block arrived last (thread 0 only).
-__device__ __forceinline__ unsigned int bar_arrive(GridSync* s, unsigned int nblocks, bool* last) {
-  unsigned int gen = ld_acquire(&s->gen);
+// Arrival (thread 0 of block gb of gn co-resident blocks).  The fence
+// publishes every write the block made before the caller's __syncthreads.
+// Returns the value the counter had before this arrival; the arrival is the
+// last one when it flipped bit 31.
+__device__ __forceinline__ unsigned int flip_arrive(GridSync* s, int gb, int gn, bool* last) {
+  const unsigned int add = gb == 0 ? 0x80000000u - (unsigned int)(gn - 1) : 1u;
   __threadfence();
-  unsigned int prev = atomicAdd(&s->count, 1u);
-  *last = (prev == nblocks - 1);
-  if (*last) __threadfence();
-  return gen;
+  const unsigned int old = atomicAdd(&s->count, add);
+  *last = ((old ^ (old + add)) & 0x80000000u) != 0;
+  return old;
 }
-__device__ __forceinline__ void bar_release(GridSync* s, unsigned int gen) {
-  s->count = 0;
-  __threadfence();
-  st_release(&s->gen, gen + 1);
-}
-__device__ __forceinline__ bool bar_wait(GridSync* s, unsigned int gen, int timeout_code) {
-  unsigned long long t0 = globaltimer();
-  while (ld_acquire(&s->gen) == gen) {
-    if (ld_volatile_int(&s->abort) != 0) return false;
-    if (globaltimer() - t0 > kWaitNs) {
-      atomicCAS(&s->abort, 0, timeout_code);
-      return false;
+
+// Bounded spin until cond() is false; checks the abort word and the time
+// limit every 64 polls.  Returns false on abort or timeout.
+template <class Cond>
+__device__ __forceinline__ bool bounded_spin(GridSync* s, int timeout_code, Cond cond) {
+  unsigned long long t0 = 0;
+  for (unsigned int it = 0; cond(); ++it) {
+    if ((it & 63u) == 63u) {
+      if (ld_volatile_int(&s->abort) != 0) return false;
+      const unsigned long long now = globaltimer();
+      if (t0 == 0) {
+        t0 = now;
+      } else if (now - t0 > kWaitNs) {
+        atomicCAS(&s->abort, 0, timeout_code);
+        return false;
+      }
+      if (it > 4096u) __nanosleep(128);  // a long wait: back off
     }
-    __nanosleep(64);
+  }
+  return true;
+}
+
+// Thread 0 of block gb: arrive and wait for all gn blocks.  The caller
+// separates the block's threads with __syncthreads on both sides; the fence
+// after the wait makes every block's earlier writes visible to this block.
+__device__ __forceinline__ bool flip_barrier(GridSync* s, int gb, int gn, int timeout_code) {
+  bool last;
+  const unsigned int old = flip_arrive(s, gb, gn, &last);
+  if (!last) {
+    const volatile unsigned int* c = &s->count;
+    if (!bounded_spin(s, timeout_code, [&] { return ((old ^ *c) & 0x80000000u) == 0; })) return false;
   }
   __threadfence();
-  return true;
+  return ld_volatile_int(&s->abort) == 0;
 }
 
 }  // namespace swe
