@@ -259,6 +259,11 @@ typedef struct {
    * (+ dots), orthogonalisation + next pass 1 (+ norm), controller tail and
    * barrier, combination, Taylor exponential, controller head */
   double phase_ms[10];
+  /* operator-table bytes the phi launches read (per cell, per IOM2 iteration
+   * and per w_j product: 62 table reals and 12 int32 neighbour indices for a
+   * pass 1 plus a pass 2), which a matrix-free stencil streams on top of the
+   * vector bytes */
+  double phi_table_bytes;
 } swe_profile;
 
 /* on != 0: zero the counters and start recording; on == 0: stop. */

@@ -53,7 +53,7 @@ class ProfileC(C.Structure):
     _fields_ = [("phi_ms", C.c_double), ("call_ms", C.c_double), ("phi_flop", C.c_double),
                 ("phi_bytes", C.c_double), ("phi_launches", C.c_int64), ("kernel_launches", C.c_int64),
                 ("iom2_iterations", C.c_int64), ("w_jv", C.c_int64), ("comb_terms", C.c_int64),
-                ("phase_ms", C.c_double * 10)]
+                ("phase_ms", C.c_double * 10), ("phi_table_bytes", C.c_double)]
 
 
 class SweError(RuntimeError):

@@ -21,6 +21,7 @@ struct DevProfile {
   long long iters, wjv, comb_terms, launches;
   long long phase_ns[10];  // block 0's time per phase class (see phi_kernel.cu)
   double flop, bytes;      // algorithmic operation count and vector bytes of the launches
+  double table_bytes;      // operator-table bytes the launches read
 };
 
 // One trace record, the same layout as the public phi_attempt.

@@ -26,7 +26,7 @@
 
 namespace swe {
 
-constexpr int PHI_MAX_THREADS = 256;  // largest block size of any instantiation
+constexpr int PHI_MAX_THREADS = 512;  // largest block size of any instantiation (sizes Shared::red)
 constexpr double TAYLOR_THETA = 4.0;
 
 // Phase classes timed by block 0 while profiling: time from the end of the
@@ -682,6 +682,8 @@ __device__ void phi_finish(const PhiArgsT<R>& a, Shared& sh) {
       a.prof->launches += 1;
       a.prof->flop += cells * (342.0 * C->n_iter + 310.0 * C->n_wjv + 8.0 * C->comb_terms);
       a.prof->bytes += cells * esz * (136.0 * C->n_iter + 104.0 * C->n_wjv + 32.0 * C->comb_terms);
+      // tables: a pass 1 and a pass 2 per IOM2 iteration and per w_j product
+      a.prof->table_bytes += cells * (62.0 * sizeof(R) + 48.0) * (double)(C->n_iter + C->n_wjv);
     }
   }
 }
@@ -793,6 +795,7 @@ int launch_ens_kernel(EnsMember* mem, const int* blk2mem, int nblocks, cudaStrea
 // least m_max + p + 1 = 69 threads.
 template <typename R, int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB) phi_kernel(const __grid_constant__ PhiArgsT<R> a) {
+  static_assert(NT % 32 == 0 && NT <= PHI_MAX_THREADS, "block size beyond the shared reduction scratch");
   __shared__ Shared sh;
   if (threadIdx.x == 0) {
     sh.gb = blockIdx.x;
@@ -812,10 +815,10 @@ static const PhiVariant kVariants[2][4] = {
      {(const void*)phi_kernel<double, 192, 2>, 192},
      {(const void*)phi_kernel<double, 128, 3>, 128},
      {(const void*)phi_kernel<double, 96, 4>, 96}},
-    {{(const void*)phi_kernel<float, 256, 2>, 256},
-     {(const void*)phi_kernel<float, 192, 2>, 192},
-     {(const void*)phi_kernel<float, 128, 3>, 128},
-     {(const void*)phi_kernel<float, 96, 4>, 96}},
+    {{(const void*)phi_kernel<float, 512, 2>, 512},
+     {(const void*)phi_kernel<float, 256, 3>, 256},
+     {(const void*)phi_kernel<float, 256, 2>, 256},
+     {(const void*)phi_kernel<float, 128, 3>, 128}},
 };
 
 // Picks the instantiation and block count for a grid of ng cells.  The FP64
@@ -823,12 +826,17 @@ static const PhiVariant kVariants[2][4] = {
 // active, so the cost of a stencil phase on the busiest SM is proportional to
 // (resident blocks) x (rounds of blockDim cells per block) x (warps per
 // block); the variant with the fewest such warp-rounds wins (ties: larger
-// blocks, fewer barriers participants).  Small grids use fewer blocks.
+// blocks, fewer barriers participants).  The FP32 stencils are bound by
+// memory latency instead (the FP32 pipe is 64x the FP64 one), so the single
+// precision variants are ranked by resident threads per SM (more loads in
+// flight), then by fewer blocks (cheaper barriers).  Small grids use fewer
+// blocks.
 int phi_select(int ng, int single, PhiLaunch* out) {
   int dev = 0, nsm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return -1;
   if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -1;
-  long long best = -1;
+  long long best = 0;
+  bool found = false;
   for (const PhiVariant& v : kVariants[single ? 1 : 0]) {
     int per = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, v.fn, v.threads, 0) != cudaSuccess || per < 1)
@@ -840,15 +848,16 @@ int phi_select(int ng, int single, PhiLaunch* out) {
     long long cells = (ng + nb - 1) / nb;
     long long rounds = (cells + v.threads - 1) / v.threads;
     long long per_sm = (nb + nsm - 1) / nsm;
-    long long cost = per_sm * rounds * (v.threads / 32);
-    if (best < 0 || cost < best) {
+    long long cost = single ? -((long long)per * v.threads * 4096 - nb) : per_sm * rounds * (v.threads / 32);
+    if (!found || cost < best) {
+      found = true;
       best = cost;
       out->fn = v.fn;
       out->threads = v.threads;
       out->nblocks = (int)nb;
     }
   }
-  return best < 0 ? -1 : 0;
+  return found ? 0 : -1;
 }
 
 // Cooperative launch (all blocks co-resident: the grid barriers need it).

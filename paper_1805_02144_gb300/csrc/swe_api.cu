@@ -1754,6 +1754,7 @@ int swe_profile_read(swe_grid* g, swe_profile* out, void* stream) {
   out->comb_terms = dp.comb_terms;
   out->phi_flop = dp.flop;
   out->phi_bytes = dp.bytes;
+  out->phi_table_bytes = dp.table_bytes;
   for (int k = 0; k < 10; ++k) out->phase_ms[k] = 1e-6 * (double)dp.phase_ns[k];
   return SWE_OK;
 }
