@@ -254,7 +254,7 @@ def batching_block() -> dict:
     E = Ensemble(gl, [c["dt"] for c in cfg], [c["nsteps"] for c in cfg], opts={"tol": TOL})
     for m, u in enumerate(u0):
         E.set_state(m, u)
-    E.tune(rounds=2)
+    E.tune(rounds=4)
 
     def reset():
         for m, u in enumerate(u0):

@@ -281,9 +281,11 @@ int swe_profile_read(swe_grid* grid, swe_profile* out, void* stream);
  * (n_m doubles, grid order); set/get copy device to device.  A run enqueues
  * two memsets and one kernel and allocates nothing, so it can be captured in
  * a CUDA graph.  The block split starts from a work model (cells x 2^level x
- * simulated time) and swe_ensemble_tune re-splits it from measured group
- * times (it runs the ensemble `rounds` times and restores the states and the
- * carried Krylov sizes).  Each member carries its last accepted Krylov size
+ * simulated time); swe_ensemble_tune runs the ensemble `rounds` times (then
+ * restores the states and the carried Krylov sizes), fits each member's group
+ * time as serial + parallel / blocks from its last two runs, re-splits to
+ * minimise the predicted longest group, and finally keeps the split whose
+ * measured longest group was shortest (3 or more rounds use the fit).  Each member carries its last accepted Krylov size
  * per call from step to step and from run to run (m carry);
  * swe_ensemble_reset clears it, as for a new trajectory.
  * opts: FP64 only (precision 0), no replay.  All grids must be device grids

@@ -1474,6 +1474,51 @@ static std::vector<int> ens_split(const std::vector<double>& w, int total) {
   return nb;
 }
 
+// Split minimising the predicted longest group time, with member m taking
+// t_m(b) = s[m] + p[m] / b on b blocks: bisection on the target time T, each
+// member getting the fewest blocks that meet T; blocks left over go, one at a
+// time, to the member predicted slowest.
+static std::vector<int> ens_split_model(const std::vector<double>& s, const std::vector<double>& p, int total) {
+  const int n = (int)s.size();
+  auto need = [&](double T, std::vector<int>& nb) {
+    long long sum = 0;
+    for (int m = 0; m < n; ++m) {
+      const double room = T - s[m];
+      long long b = room > 0.0 ? (long long)std::ceil(p[m] / room) : (long long)total + 1;
+      b = std::max(1LL, b);
+      nb[m] = (int)std::min<long long>(b, total);
+      sum += b;
+    }
+    return sum;
+  };
+  std::vector<int> nb(n, 1);
+  double lo = 0.0, hi = 0.0;
+  for (int m = 0; m < n; ++m) hi = std::max(hi, s[m] + p[m]);  // everyone on one block
+  for (int it = 0; it < 100; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (need(mid, nb) <= total)
+      hi = mid;
+    else
+      lo = mid;
+  }
+  need(hi, nb);
+  int used = std::accumulate(nb.begin(), nb.end(), 0);
+  while (used < total) {
+    int worst = 0;
+    double tw = -1.0;
+    for (int m = 0; m < n; ++m) {
+      const double t = s[m] + p[m] / nb[m];
+      if (t > tw) {
+        tw = t;
+        worst = m;
+      }
+    }
+    ++nb[worst];
+    ++used;
+  }
+  return nb;
+}
+
 extern "C" int swe_ensemble_create(swe_grid* const* grids, int nmem, const double* dt, const int* nsteps,
                                    const phi_opts* opts, swe_ensemble** out) {
   if (!grids || !dt || !nsteps || !out || nmem < 1) return fail(SWE_ERR_INVALID_ARG, "ensemble: bad arguments");
@@ -1690,6 +1735,10 @@ extern "C" int swe_ensemble_tune(swe_ensemble* E, int rounds, void* stream) {
                        cudaMemcpyDeviceToDevice, st));
   CK(cudaMemcpyAsync(E->dslots_backup, E->dslots, (size_t)2 * E->nmem * sizeof(int), cudaMemcpyDeviceToDevice, st));
   const int NB = std::accumulate(E->nb.begin(), E->nb.end(), 0);
+  // per member: the last two (blocks, ms) measurements, to fit ms = s + p / blocks
+  std::vector<std::pair<int, double>> last1(E->nmem, {0, 0.0}), last2(E->nmem, {0, 0.0});
+  std::vector<int> best_nb = E->nb;
+  double best_t = -1.0;
   for (int r = 0; r < rounds; ++r) {
     int rc = swe_ensemble_run(E, stream);
     if (rc) return rc;
@@ -1698,10 +1747,31 @@ extern "C" int swe_ensemble_tune(swe_ensemble* E, int rounds, void* stream) {
     if ((rc = swe_ensemble_stats(E, ps.data(), ms.data(), nullptr, stream))) return rc;
     for (int m = 0; m < E->nmem; ++m)
       if (ps[m].status != SWE_OK) return fail(ps[m].status, "ensemble_tune: a member failed");
-    // measured block-time of each member, then the split that equalises it
-    std::vector<double> w(E->nmem);
-    for (int m = 0; m < E->nmem; ++m) w[m] = ms[m] * E->nb[m];
-    E->nb = ens_split(w, NB);
+    const double tmax = *std::max_element(ms.begin(), ms.end());
+    if (best_t < 0.0 || tmax < best_t) {
+      best_t = tmax;
+      best_nb = E->nb;
+    }
+    std::vector<double> sv(E->nmem), pv(E->nmem);
+    for (int m = 0; m < E->nmem; ++m) {
+      last2[m] = last1[m];
+      last1[m] = {E->nb[m], ms[m]};
+      double sm = 0.0, pm = ms[m] * E->nb[m];  // one measurement: all parallel
+      const int b1 = last1[m].first, b2 = last2[m].first;
+      if (b2 > 0 && b2 != b1) {
+        const double t1 = last1[m].second, t2 = last2[m].second;
+        const double x1 = 1.0 / b1, x2 = 1.0 / b2;
+        const double pf = (t1 - t2) / (x1 - x2);
+        const double sf = t1 - pf * x1;
+        if (pf > 0.0 && sf >= 0.0) {
+          sm = sf;
+          pm = pf;
+        }
+      }
+      sv[m] = sm;
+      pv[m] = pm;
+    }
+    E->nb = ens_split_model(sv, pv, NB);
     E->nblocks = NB;
     for (int m = 0; m < E->nmem; ++m)
       CK(cudaMemcpyAsync(E->hmem[m].u, E->backup + E->state_off[m], (size_t)4 * E->grids[m]->T.ng * sizeof(double),
@@ -1709,6 +1779,10 @@ extern "C" int swe_ensemble_tune(swe_ensemble* E, int rounds, void* stream) {
     CK(cudaMemcpyAsync(E->dslots, E->dslots_backup, (size_t)2 * E->nmem * sizeof(int), cudaMemcpyDeviceToDevice, st));
     CK(cudaStreamSynchronize(st));
     if ((rc = ens_upload_split(E))) return rc;
+  }
+  if (rounds > 0) {  // keep the best split measured (the last proposal was not run)
+    E->nb = best_nb;
+    if (int rc = ens_upload_split(E)) return rc;
   }
   return SWE_OK;
 }
