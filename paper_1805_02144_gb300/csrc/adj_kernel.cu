@@ -39,8 +39,8 @@
 
 namespace swe {
 
-constexpr int ADJ_THREADS = 256;
-constexpr int ADJ_MINB = 2;
+constexpr int ADJ_THREADS = 384;
+constexpr int ADJ_MINB = 1;
 constexpr int ADJ_TAYLOR_TERMS = 32;  // the forward's Taylor degree
 constexpr int MW = KMAX + PMAX + 2;   // rows of the augmented matrix (max)
 
