@@ -810,23 +810,25 @@ struct PhiVariant {
   const void* fn;
   int threads;
 };
-static const PhiVariant kVariants[2][4] = {
-    {{(const void*)phi_kernel<double, 256, 2>, 256},
+static const PhiVariant kVariants[2][5] = {
+    {{(const void*)phi_kernel<double, 384, 1>, 384},
+     {(const void*)phi_kernel<double, 256, 2>, 256},
      {(const void*)phi_kernel<double, 192, 2>, 192},
      {(const void*)phi_kernel<double, 128, 3>, 128},
      {(const void*)phi_kernel<double, 96, 4>, 96}},
     {{(const void*)phi_kernel<float, 512, 2>, 512},
      {(const void*)phi_kernel<float, 256, 3>, 256},
      {(const void*)phi_kernel<float, 256, 2>, 256},
-     {(const void*)phi_kernel<float, 128, 3>, 128}},
+     {(const void*)phi_kernel<float, 128, 3>, 128},
+     {(const void*)phi_kernel<float, 96, 4>, 96}},
 };
 
 // Picks the instantiation and block count for a grid of ng cells.  The FP64
 // unit charges a whole warp slot per warp instruction however many lanes are
 // active, so the cost of a stencil phase on the busiest SM is proportional to
 // (resident blocks) x (rounds of blockDim cells per block) x (warps per
-// block); the variant with the fewest such warp-rounds wins (ties: larger
-// blocks, fewer barriers participants).  The FP32 stencils are bound by
+// block); the variant with the fewest such warp-rounds wins (ties: the
+// earlier, larger block, i.e. fewer barrier participants).  The FP32 stencils are bound by
 // memory latency instead (the FP32 pipe is 64x the FP64 one), so the single
 // precision variants are ranked by resident threads per SM (more loads in
 // flight), then by fewer blocks (cheaper barriers).  Small grids use fewer
