@@ -119,14 +119,16 @@ def ensemble_config(seed: int = 4, nmem: int = 64, levels=(5, 6, 7), dts=(900.0,
 
 
 def observation_network(xyz: np.ndarray, nobs: int = 1000, seed: int = 7, sigma: float = 5.0,
-                        truth_seed: int = 8, truth_amplitude: float = 400.0):
+                        truth_seed: int = 8, truth_amplitude: float = 400.0, h_truth=None):
     """Synthetic height observations for the adjoint misfit.
 
     Cells: the cell nearest to each of a seeded sequence of uniformly random
     unit vectors, duplicates dropped, until ``nobs`` distinct cells are found
     (so the set depends on positions only, not on the cell order).
-    Values: the height of a second balanced state (``truth_seed``) at those
-    cells plus Gaussian noise of standard deviation ``sigma`` [m].
+    Values: the truth height at those cells plus Gaussian noise of standard
+    deviation ``sigma`` [m].  The truth is ``h_truth`` (heights of all cells
+    in the caller's order, e.g. a truth forecast at the observation time) or,
+    when it is None, the height of the balanced state ``truth_seed``.
     Returns (cells, y, sigma) with cells indexing the caller's order.
     """
     ng = xyz.shape[0]
@@ -145,9 +147,22 @@ def observation_network(xyz: np.ndarray, nobs: int = 1000, seed: int = 7, sigma:
                 if len(cells) == nobs:
                     break
     cells = np.asarray(cells, dtype=np.int64)
-    h_truth = H0 + height_perturbation(xyz[cells], truth_seed, truth_amplitude)[0]
+    if h_truth is None:
+        h_obs = H0 + height_perturbation(xyz[cells], truth_seed, truth_amplitude)[0]
+    else:
+        h_obs = np.asarray(h_truth, dtype=np.float64)[cells]
     noise = np.random.Generator(np.random.PCG64(seed + 1)).normal(size=nobs)
-    return cells, h_truth + sigma * noise, sigma
+    return cells, h_obs + sigma * noise, sigma
+
+
+def fd_directions(u0: np.ndarray, k: int = 8, seed: int = 11, rel: float = 1e-6):
+    """k seeded standard-normal directions d_i for central differences of a
+    function of u0, each with its step eps_i = rel * ||u0|| / ||d_i||."""
+    out = []
+    for i in range(k):
+        d = random_vector(u0.size, seed + i)
+        out.append((d, rel * float(np.linalg.norm(u0)) / float(np.linalg.norm(d))))
+    return out
 
 
 def _nearest(xyz: np.ndarray, d: np.ndarray) -> np.ndarray:
