@@ -186,6 +186,22 @@ class SWE:
         """Total mass sum_i A_i h_i (the conserved quantity of Sec. 5.2)."""
         return float(np.sum(self.grid.area * self.split(u)[3]))
 
+    def energy(self, u: np.ndarray) -> float:
+        """Total energy sum_i A_i h_i (|u_i|^2/2 + g h_i/2) (conservation
+        diagnostics of the Rossby-Haurwitz section).  Reading: the paper prints
+        the density g h + |u|^2/2, which is the Bernoulli function E of
+        Eq. (eq:sweqsinv); the quantity the shallow-water equations conserve is
+        its mass-weighted form with the potential term halved, used here."""
+        ux, uy, uz, h = self.split(u)
+        return float(np.sum(self.grid.area * h * (0.5 * (ux * ux + uy * uy + uz * uz) + 0.5 * self.g * h)))
+
+    def potential_enstrophy(self, u: np.ndarray) -> float:
+        """Total potential enstrophy sum_i A_i (zeta_i + f_i)^2 / (2 h_i), with the
+        relative vorticity zeta = V . u of Eq. (eq:vort) (same section)."""
+        ux, uy, uz, h = self.split(u)
+        eta = self.vorticity(ux, uy, uz) + self.f
+        return float(np.sum(self.grid.area * eta * eta / (2.0 * h)))
+
 
 def make_swe(level: int, radius: float = EARTH_RADIUS, g: float = GRAVITY,
              omega: float = OMEGA, gamma_h: float = GAMMA_H) -> SWE:

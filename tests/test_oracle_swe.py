@@ -85,3 +85,44 @@ def test_quadratic_remainder_is_independent_of_base_state():
     assert np.linalg.norm(r1 - q) <= 1e-12 * scale
     assert np.linalg.norm(r2 - q) <= 1e-12 * scale
     assert np.linalg.norm(q) > 1e-8 * scale
+
+
+# -- conservation diagnostics (Rossby-Haurwitz section) -------------------------
+def _solid_body(s, w, H):
+    """u = w (e_z x r) (rotation about the axis with angular speed w), h = H."""
+    n = s.grid.x
+    a = s.grid.radius
+    vel = w * a * np.stack([-n[:, 1], n[:, 0], np.zeros(s.ng)], axis=1)
+    return np.concatenate([vel[:, 0], vel[:, 1], vel[:, 2], np.full(s.ng, H)])
+
+
+def test_energy_and_enstrophy_of_rest_state():
+    s = oracle_swe(4)
+    H = 5960.0
+    u = np.concatenate([np.zeros(3 * s.ng), np.full(s.ng, H)])
+    a = s.grid.radius
+    area = 4.0 * np.pi * a * a
+    assert s.energy(u) == pytest.approx(area * 0.5 * s.g * H * H, rel=1e-12)
+    # sum_i A_i f_i^2 / (2H) -> (2 Omega)^2 / (2H) * a^2 * 4 pi / 3 (quadrature error O(dx^2))
+    exact = (2.0 * s.omega) ** 2 / (2.0 * H) * a * a * 4.0 * np.pi / 3.0
+    assert s.potential_enstrophy(u) == pytest.approx(exact, rel=2e-3)
+
+
+def test_diagnostics_of_solid_body_rotation_converge_to_closed_forms():
+    """Energy and potential enstrophy of u = w e_z x r, h = H against their
+    integrals: kinetic H w^2 a^4 (4 pi/3)... via int cos^2 = 8 pi/3, and the
+    absolute vorticity (2w + 2 Omega) sin(lat) (zeta of a solid-body rotation
+    is 2 w sin(lat)), so errors shrink about fourfold per level."""
+    H, w = 5960.0, 2e-6
+    errs = []
+    for lev in (3, 4, 5):
+        s = oracle_swe(lev)
+        a = s.grid.radius
+        u = _solid_body(s, w, H)
+        e_exact = H * 0.5 * (w * a) ** 2 * a * a * 8.0 * np.pi / 3.0 + 4.0 * np.pi * a * a * 0.5 * s.g * H * H
+        z_exact = (2.0 * w + 2.0 * s.omega) ** 2 / (2.0 * H) * a * a * 4.0 * np.pi / 3.0
+        ee = abs(s.energy(u) - e_exact) / e_exact
+        ez = abs(s.potential_enstrophy(u) - z_exact) / z_exact
+        errs.append((ee, ez))
+    assert errs[-1][0] <= 1e-5 and errs[-1][1] <= 1e-3, errs
+    assert errs[2][1] < 0.5 * errs[0][1], errs      # the vorticity term converges
