@@ -92,8 +92,9 @@ def oracle_steps(nsteps: int, warmup: int) -> dict:
     return {"times": times}
 
 
-def run_oracle_subprocess(nsteps: int, warmup: int) -> dict:
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+def run_oracle_subprocess(nsteps: int, warmup: int, threads: int = 1) -> dict:
+    t = str(threads)
+    env = dict(os.environ, OMP_NUM_THREADS=t, OPENBLAS_NUM_THREADS=t, MKL_NUM_THREADS=t)
     code = (f"import json,sys; sys.path.insert(0, {ROOT!r}); import bench; "
             f"print(json.dumps(bench.oracle_steps({nsteps}, {warmup})))")
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
@@ -308,6 +309,73 @@ def batching_block() -> dict:
                                   "total": sum(st["blocks"])}}
 
 
+def schemes_block(flush) -> dict:
+    """The other schemes of the comparison on the level-7 headline grid (FP64,
+    Tol 1e-8, seed 2): exprb42 / pexprb43 / exprb53 at dt 3600 s (24 steps) and
+    epi3 at dt 900 s (96 steps), per-step CUDA events, L2 flushed between steps."""
+    import torch
+    from paper_1805_02144_gb300.api import Grid, SchemeState
+    from paper_1805_02144_gb300.inputs import balanced_state
+    G = Grid(LEVEL)
+    u0 = torch.from_numpy(balanced_state(G.cell_centres(), SEED, AMP)).cuda()
+    out = {}
+    for scheme, dt, n in (("exprb42", 3600.0, 24), ("pexprb43", 3600.0, 24), ("exprb53", 3600.0, 24),
+                          ("epi3", 900.0, 96)):
+        st = SchemeState(G)
+        ms, u, _ = timed_steps(G, u0, scheme, dt, n, {"tol": TOL}, flush, state=st)
+        tot = sum(ms)
+        out[scheme] = {"dt": dt, "steps": n, "steps_per_s": n / (tot / 1e3),
+                       "simulated_hours_per_s": n * dt / 3600.0 / (tot / 1e3),
+                       "finite": bool(torch.isfinite(u).all().item())}
+    return {"workload": "level-7 grid, FP64, Tol 1e-8, seed 2 (400 m); 24 h simulated per scheme", **out}
+
+
+def conservation_block(level: int = 4, cap_s: float = 60.0) -> dict:
+    """15 simulated days on a level-4 grid from the seeded balanced state
+    (seed 2), FP64, Tol 1e-8, with the step sizes of the paper's conservation
+    runs (exprb53 6 h, exprb42 and pexprb43 4.8 h, epi3 2 h): normalised drift
+    (X(t) - X(0)) / X(0) of total mass, energy and potential enstrophy.  A
+    scheme that fails (the trajectory can go unstable at these step sizes:
+    the same state at level 5 does for exprb53 after 14 days) or that would
+    take more than cap_s seconds stops early and says so."""
+    import time
+    import torch
+    from paper_1805_02144_gb300.api import Grid, SchemeState, exprb_step, swe_diagnostics
+    from paper_1805_02144_gb300.inputs import balanced_state
+    G = Grid(level)
+    u0 = torch.from_numpy(balanced_state(G.cell_centres(), SEED, AMP)).cuda()
+    d0 = swe_diagnostics(G, u0)
+    out = {}
+    for scheme, hours in (("exprb53", 6.0), ("exprb42", 4.8), ("pexprb43", 4.8), ("epi3", 2.0)):
+        dt = hours * 3600.0
+        n = int(round(15 * 24 / hours))
+        st = SchemeState(G)
+        u, d = u0, d0
+        worst = {k: 0.0 for k in d0}
+        status = 0
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        done = 0
+        for _ in range(n):
+            un, info = exprb_step(G, scheme, dt, u, state=st, opts={"tol": TOL}, stats=True)
+            if info["status"] != 0:
+                status = info["status"]
+                break
+            u = un
+            d = swe_diagnostics(G, u)
+            done += 1
+            for k in d0:
+                worst[k] = max(worst[k], abs(d[k] - d0[k]) / abs(d0[k]))
+            if time.perf_counter() - t0 > cap_s:
+                break
+        wall = time.perf_counter() - t0
+        out[scheme] = {"dt_hours": hours, "steps": done, "days": done * hours / 24.0, "wall_s": wall,
+                       "status": status, "drift_end": {k: (d[k] - d0[k]) / d0[k] for k in d0},
+                       "max_abs_drift": worst}
+    return {"workload": f"level-{level} grid ({G.ncells} cells), 15 days from the seeded balanced state "
+                        "(seed 2, 400 m), FP64, Tol 1e-8; diagnostics after every step", **out}
+
+
 def adjoint_block(flush) -> dict:
     """Gradient of the 6 h exprb42 forecast misfit (level 6, dt 1800 s, 12 steps,
     Tol 1e-10; observations: the 6 h truth forecast from seed 5 at 1000 seeded
@@ -501,6 +569,8 @@ def gpu_arm(args) -> None:
         line["precision"] = precision_block(flush)
         line["batching"] = batching_block()
         line["adjoint"] = adjoint_block(flush)
+        line["schemes"] = schemes_block(flush)
+        line["conservation"] = conservation_block()
     if world == 1 and not args.no_cpu_baseline:
         try:
             res = run_oracle_subprocess(1, 0)
@@ -512,6 +582,16 @@ def gpu_arm(args) -> None:
         except Exception as e:  # report, do not hide
             line["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
                                     "sample": f"failed: {e!s:.200}"}
+        try:  # the same with every host core available to numpy / scipy / BLAS threads
+            ncore = os.cpu_count() or 1
+            res = run_oracle_subprocess(1, 0, ncore)
+            line["cpu_baseline_all_cores"] = {
+                "value": 1.0 / res["times"][0], "unit": UNIT, "cores": ncore, "kind": "oracle",
+                "sample": "the same step with OMP/BLAS threads = host cores (the oracle's sparse "
+                          "products are single-threaded, so this bounds what threads buy it)"}
+        except Exception as e:
+            line["cpu_baseline_all_cores"] = {"value": None, "unit": UNIT, "kind": "oracle",
+                                              "sample": f"failed: {e!s:.200}"}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -525,7 +605,7 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the precision/batching/adjoint blocks")
-    ap.add_argument("--only", choices=["precision", "batching", "adjoint"],
+    ap.add_argument("--only", choices=["precision", "batching", "adjoint", "schemes", "conservation"],
                     help="run one extra block alone and print it (for profiling)")
     args = ap.parse_args()
     if args.only:
@@ -534,7 +614,8 @@ def main():
         build.build()
         flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
         fn = {"precision": lambda: precision_block(flush), "batching": batching_block,
-              "adjoint": lambda: adjoint_block(flush)}[args.only]
+              "adjoint": lambda: adjoint_block(flush), "schemes": lambda: schemes_block(flush),
+              "conservation": conservation_block}[args.only]
         print(json.dumps({args.only: fn()}), flush=True)
         return
     if args.impl == "reference":

@@ -72,6 +72,10 @@ typedef struct {
                         most a few dozen terms, then FP64), norms, controller and
                         exponential in FP64; F(u_n), D_ni and the state update in
                         FP64.  Public vectors stay FP64 either way.                 */
+  int max_substeps;  /* SWE_ERR_NOCONV when one call needs more accepted substeps
+                        (default 4096), or when an accepted substep would not move
+                        t; bounds the run time of a launch whose step sizes the
+                        controller has driven towards zero                      */
 } phi_opts;
 
 /* One controller attempt (trace record). */
@@ -166,6 +170,17 @@ int swe_jv(const swe_grid* grid, const double* u, const double* x, double* jx, v
  * calls that overlap on the GPU (e.g. on two streams) race and must be
  * serialised by the caller.  u, x, jx: device, n doubles; jx distinct. */
 int swe_jv_noalloc(const swe_grid* grid, const double* u, const double* x, double* jx, void* stream);
+
+/* Conservation diagnostics of the Rossby-Haurwitz section (total mass,
+ * total energy and potential enstrophy of a state): out_host[0] =
+ * sum_i A_i h_i, out_host[1] = sum_i A_i h_i (|u_i|^2/2 + g h_i/2),
+ * out_host[2] = sum_i A_i (zeta_i + f_i)^2 / (2 h_i), zeta = V.u of Eq. eq:vort.
+ * (Reading: the paper prints the energy density g h + |u|^2/2, the Bernoulli
+ * function; the conserved total energy is the mass-weighted form with the
+ * potential term halved.)  Summed per block and then over blocks in a fixed
+ * order, so the result is reproducible.  u: device, n doubles; out_host:
+ * host, 3 doubles.  Waits for the stream. */
+int swe_diagnostics(const swe_grid* grid, const double* u, double* out_host, void* stream);
 
 /* out = J(u)^T lam, the transpose of the Jacobian of Eqs. eq:dynja-eq:dynjc
  * (the operator the adjoint of a step applies; the paper defines J, its

@@ -54,6 +54,11 @@ R9  Substeps land exactly on each rho_i: tau_k = rho_i - t_k whenever
     and accepted, the next step size is max(tau_new, tau) so the shortening
     does not shrink later substeps.  tau and m carry over to the next output.
 R10 Zero skip (step 1): A w_{j-1} is skipped when w_{j-1} is exactly zero.
+R11 Bounds (not in the paper): a call fails with NoConvergence after
+    max_substeps accepted substeps, when an accepted substep would not move
+    t, or when ||tau Hhat_m||_1 exceeds HNORM_MAX = 4096 (the GPU's scaled
+    Taylor exponential would need more than 1024 scaling steps), so a run
+    whose state or step size has gone wrong ends instead of running on.
 """
 from __future__ import annotations
 
@@ -70,6 +75,9 @@ class NoConvergence(RuntimeError):
     pass
 
 
+HNORM_MAX = 4096.0   # R11
+
+
 @dataclasses.dataclass
 class PhiOpts:
     tol: float = 1e-8
@@ -81,6 +89,7 @@ class PhiOpts:
     gamma: float = 0.8                # R8
     kappa: float = 2.0                # R8
     max_reject: int = 200
+    max_substeps: int = 4096          # NoConvergence beyond this many accepted substeps per call
     breakdown: float = 1e-13          # R4
 
 
@@ -223,13 +232,17 @@ def phipm_simul_iom2(Amul: Callable[[np.ndarray], np.ndarray],
                     m_use = basis.extend(m)
                     Hm = basis.H[0:m_use, 0:m_use]
                     hnext = basis.H[m_use, m_use - 1]
+                    hnorm = augmented_norm1(Hm, tau_k, p)
+                    if not hnorm <= HNORM_MAX:
+                        raise NoConvergence(f"phipm_simul_iom2: ||tau Hhat||_1 = {hnorm} beyond {HNORM_MAX}")
                     phi_p, phi_p1 = phi_krylov(Hm, tau_k, p)
                     eps = tau_k ** p * beta * tau_k * abs(hnext) * abs(phi_p1[m_use - 1])  # R6
-                    hnorm = augmented_norm1(Hm, tau_k, p)
                 else:
                     m_use, eps, hnorm = m, 0.0, 1.0
                 # step 6 test (R7)
                 omega = t_out * eps / (tau_k * opts.tol * scale)
+                if not math.isfinite(omega):
+                    raise NoConvergence("phipm_simul_iom2: non-finite error estimate")
                 accepted = omega <= opts.delta if rp is None else rec.accepted
                 stats.trace.append(Attempt(t=t, tau=tau_k, m=m_use, omega=omega, accepted=accepted))
                 stats.m_max_used = max(stats.m_max_used, m_use)
@@ -263,7 +276,10 @@ def phipm_simul_iom2(Amul: Callable[[np.ndarray], np.ndarray],
                         krylov = krylov + tau_k * hnext * phi_p1[m_use - 1] * basis.V[m_use]
                         ynew = ynew + (tau_k ** p * beta) * krylov
                     y = ynew
-                    t = t_out if land else t + tau_k
+                    t_next = t_out if land else t + tau_k
+                    if not t_next > t or stats.n_substeps >= opts.max_substeps:
+                        raise NoConvergence(f"phipm_simul_iom2: {stats.n_substeps} substeps, no progress at t={t}")
+                    t = t_next
                     stats.n_substeps += 1
                     if take_tau:
                         tau = max(tau_new, tau) if land else tau_new

@@ -112,6 +112,14 @@ def swe_jv(grid: Grid, u: torch.Tensor, x: torch.Tensor, out: Optional[torch.Ten
     return out
 
 
+def swe_diagnostics(grid: Grid, u: torch.Tensor, stream=None) -> dict:
+    """Total mass, energy and potential enstrophy of a state (see the header)."""
+    out = np.zeros(3)
+    check(load().swe_diagnostics(grid.handle, _ptr(u, grid.n, "u"), out.ctypes.data_as(C.POINTER(C.c_double)),
+                                 _stream(stream)))
+    return {"mass": float(out[0]), "energy": float(out[1]), "potential_enstrophy": float(out[2])}
+
+
 def swe_jtv(grid: Grid, u: torch.Tensor, lam: torch.Tensor, out: Optional[torch.Tensor] = None,
             stream=None) -> torch.Tensor:
     """out = J(u)^T lam (transpose of the Jacobian of Eqs. (eq:dynja)-(eq:dynjc))."""

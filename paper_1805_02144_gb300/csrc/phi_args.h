@@ -106,7 +106,7 @@ struct PhiArgsT {
   int tape_cap;             // accepted substeps the tape holds
   // options
   double tol, delta, gamma, kappa;
-  int tol_mode, m_init, m_max, max_reject;
+  int tol_mode, m_init, m_max, max_reject, max_substeps;
   int64_t nA;
 };
 using PhiArgs = PhiArgsT<double>;

@@ -28,6 +28,10 @@ namespace swe {
 
 constexpr int PHI_MAX_THREADS = 512;  // largest block size of any instantiation (sizes Shared::red)
 constexpr double TAYLOR_THETA = 4.0;
+// Largest ||tau Hhat||_1 the scaled Taylor evaluation accepts (1024 scaling
+// steps); beyond it (or when it is not finite) the call fails with NOCONV, as
+// it only happens for states or step sizes that have already gone wrong.
+constexpr double HNORM_MAX = 1024.0 * TAYLOR_THETA;
 
 // Phase classes timed by block 0 while profiling: time from the end of the
 // previous barrier to the end of this one (work plus wait).
@@ -232,6 +236,13 @@ __device__ void decide(const A& a, Shared& sh) {
     }
     __syncthreads();
     hnorm = fmax(tau_k * sh.scal[0], 1.0);
+    if (!(hnorm <= HNORM_MAX)) {  // uniform in the block: every lane sees the same value
+      if (lane == 0) {
+        C->status = SWE_ERR_NOCONV;
+        abort_launch(a, SWE_ERR_NOCONV);
+      }
+      return;
+    }
     phase_tick(a, sh, PH_CONTROL);
     taylor_phi(sh, m_use, p, tau_k, hnorm);
     phase_tick(a, sh, PH_TAYLOR);
@@ -336,7 +347,13 @@ __device__ void decide(const A& a, Shared& sh) {
     }
     C->ncomb = beta > 0.0 ? m_use + 1 : 0;
     C->comb_terms += C->ncomb + p;
-    C->t = land ? t_out : t + tau_k;
+    const double t_next = land ? t_out : t + tau_k;
+    if (!(t_next > t) || C->n_sub >= a.max_substeps) {  // no progress, or too many substeps
+      C->status = SWE_ERR_NOCONV;
+      abort_launch(a, SWE_ERR_NOCONV);
+      return;
+    }
+    C->t = t_next;
     C->n_sub += 1;
     if (take_tau) {
       C->tau = land ? fmax(tau_new, tau_nom) : tau_new;

@@ -186,6 +186,56 @@ __global__ void k_pass2T(Tables T, const double* lam, const double* u, const dou
   }
 }
 
+// Conservation diagnostics: per block, in a fixed order, the sums of
+// A_i h_i, A_i h_i (|u_i|^2/2 + g h_i/2) and A_i (zeta_i + f_i)^2 / (2 h_i).
+constexpr int DIAG_THREADS = 256;
+__global__ void __launch_bounds__(DIAG_THREADS) k_diag(Tables T, const double* __restrict__ u, double* part) {
+  __shared__ double red[3][DIAG_THREADS / 32];
+  const int ng = T.ng;
+  double m = 0.0, e = 0.0, z = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ng; i += gridDim.x * blockDim.x) {
+    int nb[SLOTS];
+    load_nbr(T, i, nb);
+    double vor = 0.0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) vor = fma(ldtab(T.vd + (size_t)c * ng + i), u[(size_t)c * ng + i], vor);
+#pragma unroll
+    for (int k = 0; k < SLOTS; ++k)
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+        vor = fma(ldtab(T.vc + ((size_t)c * SLOTS + k) * ng + i), u[(size_t)c * ng + nb[k]], vor);
+    const double eta = fma(T.two_omega, ldtab(T.nrm + 2 * (size_t)ng + i), vor);
+    const double u0 = u[i], u1 = u[(size_t)ng + i], u2 = u[2 * (size_t)ng + i], h = u[3 * (size_t)ng + i];
+    const double A = T.area[i];
+    m = fma(A, h, m);
+    e = fma(A * h, fma(0.5, fma(u0, u0, fma(u1, u1, u2 * u2)), 0.5 * T.g * h), e);
+    z = fma(A, eta * eta / (2.0 * h), z);
+  }
+  double v[3] = {m, e, z};
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+    if (lane == 0) red[k][warp] = v[k];
+  }
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    double s = 0.0;
+    for (int w = 0; w < DIAG_THREADS / 32; ++w) s += red[threadIdx.x][w];
+    part[(size_t)blockIdx.x * 3 + threadIdx.x] = s;
+  }
+}
+
+// Sum of the block partials in block order (one thread per quantity).
+__global__ void k_diag_sum(const double* part, int nblocks, double* out) {
+  if (threadIdx.x < 3) {
+    double s = 0.0;
+    for (int b = 0; b < nblocks; ++b) s += part[(size_t)b * 3 + threadIdx.x];
+    out[threadIdx.x] = s;
+  }
+}
+
 struct Comb {
   const double* x[6];
   double c[6];
@@ -302,7 +352,7 @@ int upload_grid(swe_grid* g) {
   const int32_t* d_nbr = nullptr;
   const double *d_nrm = nullptr, *d_wl = nullptr, *d_wld = nullptr, *d_nc = nullptr, *d_ndd = nullptr,
                *d_sdg = nullptr, *d_vc = nullptr, *d_vd = nullptr, *d_wlT = nullptr, *d_ncT = nullptr,
-               *d_vcT = nullptr;
+               *d_vcT = nullptr, *d_area = nullptr;
   // the kernels read the G diagonal ndd - sdg directly (table "sdg" of the
   // device copy holds that difference)
   std::vector<double> gdg(h.sdg.size());
@@ -314,6 +364,7 @@ int upload_grid(swe_grid* g) {
       {gdg.data(), gdg.size() * 8, (void**)&d_sdg},  {h.vc.data(), h.vc.size() * 8, (void**)&d_vc},
       {h.vd.data(), h.vd.size() * 8, (void**)&d_vd},     {h.wlT.data(), h.wlT.size() * 8, (void**)&d_wlT},
       {h.ncT.data(), h.ncT.size() * 8, (void**)&d_ncT},  {h.vcT.data(), h.vcT.size() * 8, (void**)&d_vcT},
+      {h.area.data(), h.area.size() * 8, (void**)&d_area},
   };
   size_t total = 0;
   for (auto& p : parts) total += (p.bytes + 255) & ~size_t(255);
@@ -340,6 +391,7 @@ int upload_grid(swe_grid* g) {
   T.wlT = d_wlT;
   T.ncT = d_ncT;
   T.vcT = d_vcT;
+  T.area = d_area;
   return SWE_OK;
 }
 
@@ -444,7 +496,7 @@ int resolve_opts(const phi_opts* in, phi_opts& o) {
   else
     swe_phi_opts_default(&o);
   if (!(o.tol > 0.0) || o.m_init < 1 || o.m_max < 1 || o.m_max > KMAX || o.iom != 2 ||
-      !(o.delta > 0.0) || !(o.gamma > 0.0) || !(o.kappa > 1.0) || o.max_reject < 0 ||
+      !(o.delta > 0.0) || !(o.gamma > 0.0) || !(o.kappa > 1.0) || o.max_reject < 0 || o.max_substeps < 1 ||
       (o.tol_mode != 0 && o.tol_mode != 1) || (o.replay && o.n_replay < 1) ||
       (o.precision != 0 && o.precision != 1))
     return fail(SWE_ERR_INVALID_ARG, "invalid phi_opts (m_max <= 64, iom == 2, tol > 0, kappa > 1)");
@@ -514,6 +566,7 @@ void fill_phi_args(swe_grid* g, A& a, double dt, int p, int ns, const double* rh
   a.m_init = o.m_init;
   a.m_max = o.m_max;
   a.max_reject = o.max_reject;
+  a.max_substeps = o.max_substeps;
   a.nA = g->host.nA;
   a.prof = g->prof_on ? g->dprof : nullptr;
 }
@@ -895,6 +948,7 @@ void swe_phi_opts_default(phi_opts* o) {
   o->gamma = 0.8;
   o->kappa = 2.0;
   o->max_reject = 200;
+  o->max_substeps = 4096;
   o->m_carry = 1;
   o->replay = nullptr;
   o->n_replay = 0;
@@ -1026,6 +1080,25 @@ int swe_jv(const swe_grid* gc, const double* u, const double* x, double* jx, voi
   k_pass2<MODE_J><<<nb, TPB, 0, st>>>(T, x, 1.0, g->tmp2, g->aux, 1.0, jx);
   CK(cudaGetLastError());
   count_launches(g, 3);
+  return SWE_OK;
+}
+
+int swe_diagnostics(const swe_grid* gc, const double* u, double* out_host, void* stream) {
+  swe_grid* g = const_cast<swe_grid*>(gc);
+  if (!g || !u || !out_host) return fail(SWE_ERR_INVALID_ARG, "swe_diagnostics: NULL argument");
+  int rc = ensure_workspace(g);
+  if (rc) return rc;
+  cudaStream_t st = S(stream);
+  const int nb = std::min(grid_blocks(g->T.ng), 4 * 152);
+  double* part = g->tmp2;              // nb x 3 partials (tmp2 holds 8 ng doubles)
+  double* res = g->tmp2 + (size_t)3 * nb;
+  if ((size_t)3 * nb + 3 > (size_t)8 * g->T.ng) return fail(SWE_ERR_INVALID_ARG, "swe_diagnostics: grid too small");
+  k_diag<<<nb, DIAG_THREADS, 0, st>>>(g->T, u, part);
+  k_diag_sum<<<1, 32, 0, st>>>(part, nb, res);
+  CK(cudaGetLastError());
+  count_launches(g, 2);
+  CK(cudaMemcpyAsync(out_host, res, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
   return SWE_OK;
 }
 
@@ -1636,6 +1709,7 @@ extern "C" int swe_ensemble_create(swe_grid* const* grids, int nmem, const doubl
       a.m_init = o.m_init;
       a.m_max = o.m_max;
       a.max_reject = o.max_reject;
+      a.max_substeps = o.max_substeps;
       a.nA = g->host.nA;
     }
     M.c1.p = 1;

@@ -26,6 +26,7 @@ struct TablesT {
   const R* __restrict__ gdg;   // [3][ng] G diagonal (ndd - sdg of the host tables)
   const R* __restrict__ vc;    // [3][6][ng]
   const R* __restrict__ vd;    // [3][ng]
+  const R* __restrict__ area;  // [ng] cell areas A_i (FP64 grids only)
   // transposed slot tables (FP64 grids only; see grid_build.h)
   const R* __restrict__ wlT;   // [6][ng]
   const R* __restrict__ ncT;   // [3][6][ng]

@@ -136,6 +136,31 @@ def test_phi_action_reports_no_convergence():
     assert gst["status"] == 0
 
 
+@pytest.mark.parametrize("case", ["substeps", "exponent"])
+def test_phi_action_bounds_end_runaway_calls(case):
+    """A call that would need more than max_substeps accepted substeps, or an
+    exponential of ||tau Hhat||_1 beyond 4096 (a state or step size gone
+    wrong), ends with NOCONV like the oracle's NoConvergence, and the grid
+    stays usable."""
+    from oracle.phipm import NoConvergence
+    from paper_1805_02144_gb300.api import phi_action
+    G, s, idx = pair(3)
+    u = _state(s, 1, 200.0)
+    x = random_vector(s.n, 3)
+    if case == "substeps":
+        dt, gopts, oopts = 3600.0, {"max_substeps": 1, "m_max": 4}, PhiOpts(max_substeps=1, m_max=4)
+    else:
+        dt, gopts, oopts = 1e9, {}, PhiOpts()
+    with pytest.raises(NoConvergence):
+        phipm_simul_iom2(lambda y: dt * s.Jv(u, y), [1.0], [None, x], oopts, s.nA)
+    outs, gst = phi_action(G, dev(to_prod(u, idx)), dt, [None, dev(to_prod(x, idx))], [1.0],
+                           opts=gopts, stats=True)
+    assert gst["status"] == -3
+    outs, gst = phi_action(G, dev(to_prod(u, idx)), 900.0, [None, dev(to_prod(x, idx))], [1.0],
+                           stats=True)
+    assert gst["status"] == 0
+
+
 @pytest.mark.parametrize("scheme,lev,dt,nsteps", [
     ("exprb42", 3, 900.0, 1),          # the level-3 exprb42 single-step workload
     ("exprb42", 3, 3600.0, 3),
