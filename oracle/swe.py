@@ -12,7 +12,10 @@ variable, nu from Eq. (eq:niu):
     du_c/dt = -eta * P_c - G_c E - nu L(L u_c),        c = x, y, z
     dh/dt   = -(D_x (u_x h) + D_y (u_y h) + D_z (u_z h)) - nu L(L h)
     eta = V_x u_x + V_y u_y + V_z u_z + f,  f = 2 Omega n_z,  P = n x u,
-    E   = (u_x^2 + u_y^2 + u_z^2)/2 + g (h + h_s),  h_s = 0.
+    E   = (u_x^2 + u_y^2 + u_z^2)/2 + g (h + h_s),  h_s = 0 unless given.
+
+With topography (``hs``, the surface height h_s per cell, constant in time)
+only E changes: F gains -G (g h_s); J(u) does not depend on h_s.
 
 The Jacobian J = J_v + J_r + J_m is applied block by block as printed in
 Eqs. (eq:dynja)-(eq:dynjc).  Reading: the second row of J_r is printed as
@@ -52,6 +55,7 @@ class SWE:
     g: float = GRAVITY
     omega: float = OMEGA
     gamma_h: float = GAMMA_H
+    hs: np.ndarray = None          # surface height h_s per cell [m] (None = 0)
 
     @property
     def ng(self) -> int:
@@ -103,6 +107,8 @@ class SWE:
         eta = self.vorticity(ux, uy, uz) + self.f
         P = self.cross_n(ux, uy, uz)
         E = 0.5 * (ux * ux + uy * uy + uz * uz) + self.g * h
+        if self.hs is not None:
+            E = E + self.g * self.hs
         out = np.empty_like(u)
         ng = self.ng
         for c, uc in enumerate((ux, uy, uz)):

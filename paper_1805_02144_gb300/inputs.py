@@ -170,3 +170,10 @@ def _nearest(xyz: np.ndarray, d: np.ndarray) -> np.ndarray:
     for a in range(0, d.shape[0], 64):
         out[a:a + 64] = np.argmax(d[a:a + 64] @ xyz.T, axis=1)
     return out
+
+
+def topography(xyz: np.ndarray, seed: int = 9, height: float = 2000.0) -> np.ndarray:
+    """A smooth seeded surface height h_s in [0, height] [m]: (height + h') / 2
+    with h' the sinusoid sum above (amplitude ``height``, seed ``seed``)."""
+    hp, _ = height_perturbation(np.asarray(xyz, dtype=np.float64), seed, height)
+    return 0.5 * (height + hp)

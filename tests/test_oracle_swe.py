@@ -126,3 +126,42 @@ def test_diagnostics_of_solid_body_rotation_converge_to_closed_forms():
         errs.append((ee, ez))
     assert errs[-1][0] <= 1e-5 and errs[-1][1] <= 1e-3, errs
     assert errs[2][1] < 0.5 * errs[0][1], errs      # the vorticity term converges
+
+
+# -- topography -------------------------------------------------------------
+def _with_hs(s, hs):
+    import dataclasses
+    return dataclasses.replace(s, hs=hs)
+
+
+def test_topography_enters_F_through_the_gradient_only():
+    """F(u; h_s) - F(u; 0) = (-G_c(g h_s), 0) exactly, and J does not change."""
+    from paper_1805_02144_gb300.inputs import topography
+    s = oracle_swe(3)
+    hs = topography(s.grid.x, 9, 2000.0)
+    st = _with_hs(s, hs)
+    u = balanced_state(s.grid.x, 2, 300.0)
+    dF = st.F(u) - s.F(u)
+    ng = s.ng
+    for c in range(3):
+        ref = -(s.ops.G[c] @ (s.g * hs))
+        assert np.abs(dF[c * ng:(c + 1) * ng] - ref).max() <= 1e-12 * np.abs(ref).max()
+    assert np.abs(dF[3 * ng:]).max() == 0.0
+    x = random_vector(s.n, 3)
+    assert np.array_equal(st.Jv(u, x), s.Jv(u, x))
+
+
+def test_lake_at_rest_over_topography_has_no_momentum_tendency():
+    """u = 0, h + h_s = const: the pressure gradient of a constant vanishes
+    (edge values of a constant are that constant), so F_u = 0 to rounding;
+    only the hyperdiffusion of h remains in F_h."""
+    from paper_1805_02144_gb300.inputs import topography
+    s = oracle_swe(4)
+    hs = topography(s.grid.x, 9, 2000.0)
+    st = _with_hs(s, hs)
+    u = np.concatenate([np.zeros(3 * s.ng), 5960.0 - hs])
+    F = st.F(u)
+    scale = np.abs(s.ops.G[0] @ (s.g * hs)).max()     # the size of either gradient alone
+    assert np.abs(F[:3 * s.ng]).max() <= 1e-12 * scale
+    assert np.abs(F[3 * s.ng:] - (-s.nu * (s.ops.L @ (s.ops.L @ u[3 * s.ng:])))).max() \
+        <= 1e-12 * np.abs(F[3 * s.ng:]).max()
