@@ -171,6 +171,13 @@ int swe_jv(const swe_grid* grid, const double* u, const double* x, double* jx, v
  * serialised by the caller.  u, x, jx: device, n doubles; jx distinct. */
 int swe_jv_noalloc(const swe_grid* grid, const double* u, const double* x, double* jx, void* stream);
 
+/* Surface height h_s (Sec. 2: E = |u|^2/2 + g (h + h_s) in Eq. eq:sweqsinv):
+ * hs_host is a host array of ncells doubles [m] in the grid's order, copied
+ * to the device; NULL removes it (h_s = 0, the default).  Only F changes
+ * (J does not depend on h_s).  Waits for the device.  Ensembles copy the
+ * grid's tables when created, so set the topography first. */
+int swe_grid_set_topography(swe_grid* grid, const double* hs_host);
+
 /* Conservation diagnostics of the Rossby-Haurwitz section (total mass,
  * total energy and potential enstrophy of a state): out_host[0] =
  * sum_i A_i h_i, out_host[1] = sum_i A_i h_i (|u_i|^2/2 + g h_i/2),

@@ -77,6 +77,7 @@ class TorchSWE:
         self.nu = swe.nu
         self.g = swe.g
         self.nA = swe.nA
+        self.hs = None if swe.hs is None else torch.from_numpy(np.asarray(swe.hs, dtype=np.float64))
         L = swe.ops.L
         self.LL = (L @ L).tocsr()
 
@@ -101,6 +102,8 @@ class TorchSWE:
         eta = self.vorticity(ux, uy, uz) + self.f
         P = self.cross_n(ux, uy, uz)
         E = 0.5 * (ux * ux + uy * uy + uz * uz) + self.g * h
+        if self.hs is not None:
+            E = E + self.g * self.hs
         parts = [-eta * P[c] - spmv(G[c], E) + self.Df(uc) for c, uc in enumerate((ux, uy, uz))]
         parts.append(-(spmv(D[0], ux * h) + spmv(D[1], uy * h) + spmv(D[2], uz * h)) + self.Df(h))
         return torch.cat(parts)

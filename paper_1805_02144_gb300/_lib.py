@@ -22,7 +22,7 @@ SCHEMES = {"epi2": 0, "exprb42": 1, "pexprb43": 2, "exprb53": 3, "epi3": 4}
 EXPORTS = ["swe_phi_opts_default", "swe_create_grid", "swe_create_grid_host", "swe_grid_export",
            "swe_destroy_grid", "swe_grid_query",
            "swe_grid_cell_centres", "swe_grid_cell_areas", "swe_rhs", "swe_jv", "swe_jv_noalloc",
-           "swe_jtv", "swe_dqtv", "swe_diagnostics", "phi_action",
+           "swe_jtv", "swe_dqtv", "swe_diagnostics", "swe_grid_set_topography", "phi_action",
            "swe_scheme_state_create", "swe_scheme_state_reset", "swe_scheme_state_destroy",
            "exprb_step", "exprb_step_adjoint", "swe_profile_enable", "swe_profile_read", "swe_device_status",
            "swe_last_error", "swe_ensemble_create", "swe_ensemble_destroy", "swe_ensemble_set_state",
@@ -95,6 +95,7 @@ def load(path: Optional[str] = None) -> C.CDLL:
     L.swe_jv_noalloc.argtypes = [vp, vp, vp, vp, vp]
     L.swe_jtv.argtypes = [vp, vp, vp, vp, vp]
     L.swe_diagnostics.argtypes = [vp, vp, dp, vp]
+    L.swe_grid_set_topography.argtypes = [vp, dp]
     L.swe_dqtv.argtypes = [vp, vp, vp, vp, vp]
     L.phi_action.argtypes = [vp, vp, C.c_double, C.c_int, C.POINTER(vp), C.c_int, dp, C.POINTER(vp),
                              C.POINTER(PhiOptsC), C.POINTER(PhiStatsC), vp]
@@ -122,7 +123,7 @@ def load(path: Optional[str] = None) -> C.CDLL:
     L.swe_last_error.argtypes = []
     L.swe_last_error.restype = C.c_char_p
     for name in ("swe_create_grid", "swe_create_grid_host", "swe_grid_export", "swe_grid_query", "swe_grid_cell_centres", "swe_grid_cell_areas",
-                 "swe_rhs", "swe_jv", "swe_jv_noalloc", "swe_jtv", "swe_dqtv", "swe_diagnostics", "phi_action",
+                 "swe_rhs", "swe_jv", "swe_jv_noalloc", "swe_jtv", "swe_dqtv", "swe_diagnostics", "swe_grid_set_topography", "phi_action",
                  "swe_scheme_state_create",
                  "swe_scheme_state_reset", "exprb_step", "exprb_step_adjoint", "swe_device_status", "swe_profile_enable",
                  "swe_profile_read", "swe_ensemble_create", "swe_ensemble_set_state",

@@ -112,6 +112,17 @@ def swe_jv(grid: Grid, u: torch.Tensor, x: torch.Tensor, out: Optional[torch.Ten
     return out
 
 
+def swe_grid_set_topography(grid: Grid, hs: Optional[np.ndarray]) -> None:
+    """Set (or, with None, remove) the surface height h_s [m] per cell (grid order)."""
+    if hs is None:
+        check(load().swe_grid_set_topography(grid.handle, None))
+        return
+    a = np.ascontiguousarray(np.asarray(hs, dtype=np.float64))
+    if a.size != grid.ncells:
+        raise ValueError("hs needs one value per cell")
+    check(load().swe_grid_set_topography(grid.handle, a.ctypes.data_as(C.POINTER(C.c_double))))
+
+
 def swe_diagnostics(grid: Grid, u: torch.Tensor, stream=None) -> dict:
     """Total mass, energy and potential enstrophy of a state (see the header)."""
     out = np.zeros(3)

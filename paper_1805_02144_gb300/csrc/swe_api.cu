@@ -106,6 +106,7 @@ struct swe_grid {
   size_t hstage_cap = 0;
   cudaEvent_t stage_ev = nullptr;
   int* adj_status = nullptr;    // device: first error of the adjoint launches of a step
+  double* dhs = nullptr;        // surface height h_s (device), when set
 };
 
 struct swe_ensemble {
@@ -1035,6 +1036,7 @@ void swe_destroy_grid(swe_grid* g) {
   if (g->dtape) cudaFree(g->dtape);
   if (g->hstage) cudaFreeHost(g->hstage);
   if (g->stage_ev) cudaEventDestroy(g->stage_ev);
+  if (g->dhs) cudaFree(g->dhs);
   delete g;
 }
 
@@ -1080,6 +1082,29 @@ int swe_jv(const swe_grid* gc, const double* u, const double* x, double* jx, voi
   k_pass2<MODE_J><<<nb, TPB, 0, st>>>(T, x, 1.0, g->tmp2, g->aux, 1.0, jx);
   CK(cudaGetLastError());
   count_launches(g, 3);
+  return SWE_OK;
+}
+
+int swe_grid_set_topography(swe_grid* g, const double* hs_host) {
+  if (!g) return fail(SWE_ERR_INVALID_ARG, "swe_grid_set_topography: NULL grid");
+  if (!g->dtab) return fail(SWE_ERR_INVALID_ARG, "grid was built on the host only");
+  CK(cudaDeviceSynchronize());  // no work in flight reads the old field
+  if (!hs_host) {
+    if (g->dhs) cudaFree(g->dhs);
+    g->dhs = nullptr;
+    g->T.hs = nullptr;
+    return SWE_OK;
+  }
+  const size_t bytes = (size_t)g->T.ng * sizeof(double);
+  if (!g->dhs) {
+    cudaError_t e = cudaMalloc(&g->dhs, bytes);
+    if (e != cudaSuccess) {
+      g->dhs = nullptr;
+      return fail(SWE_ERR_NOMEM, std::string("topography allocation failed: ") + cudaGetErrorString(e));
+    }
+  }
+  CK(cudaMemcpy(g->dhs, hs_host, bytes, cudaMemcpyHostToDevice));
+  g->T.hs = g->dhs;
   return SWE_OK;
 }
 

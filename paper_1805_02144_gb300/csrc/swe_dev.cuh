@@ -27,6 +27,7 @@ struct TablesT {
   const R* __restrict__ vc;    // [3][6][ng]
   const R* __restrict__ vd;    // [3][ng]
   const R* __restrict__ area;  // [ng] cell areas A_i (FP64 grids only)
+  const R* __restrict__ hs;    // [ng] surface height h_s, or nullptr (none)
   // transposed slot tables (FP64 grids only; see grid_build.h)
   const R* __restrict__ wlT;   // [6][ng]
   const R* __restrict__ ncT;   // [3][6][ng]
@@ -90,7 +91,7 @@ __device__ __forceinline__ void load_nbr(const TablesT<R>& T, int i, int (&nb)[S
 
 // Pass 1 of a stencil at cell i.  Writes four Laplacian planes to Lout and
 // the scalar and vector planes to sq (4 planes: scalar, vector x, y, z):
-//   MODE_F: x = u.          L u (4), E = |u|^2/2 + g h, q = u h
+//   MODE_F: x = u.          L u (4), E = |u|^2/2 + g (h + h_s), q = u h
 //   MODE_J: x = sx * xraw.  L x (4), s = u.x_u + g x_h,  q = x_u h + u x_h
 //   MODE_Q: x = d.          -,       E = |d_u|^2/2,      q = d_u d_h
 template <int MODE, typename R>
@@ -119,7 +120,8 @@ __device__ __forceinline__ void pass1_cell(const TablesT<R>& T, int i, const R* 
 #pragma unroll
     for (int c = 0; c < 3; ++c) sq[(size_t)(1 + c) * ng + i] = fma(xv[c], uv[3], uv[c] * xv[3]);
   } else if (MODE == MODE_F) {
-    sq[i] = fma(R(0.5), fma(xv[0], xv[0], fma(xv[1], xv[1], xv[2] * xv[2])), T.g * xv[3]);
+    const R hsurf = T.hs ? ld(T.hs + i) : R(0);  // E = |u|^2/2 + g (h + h_s)
+    sq[i] = fma(R(0.5), fma(xv[0], xv[0], fma(xv[1], xv[1], xv[2] * xv[2])), T.g * (xv[3] + hsurf));
 #pragma unroll
     for (int c = 0; c < 3; ++c) sq[(size_t)(1 + c) * ng + i] = xv[c] * xv[3];
   } else {
