@@ -330,6 +330,48 @@ def schemes_block(flush) -> dict:
     return {"workload": "level-7 grid, FP64, Tol 1e-8, seed 2 (400 m); 24 h simulated per scheme", **out}
 
 
+def efficiency_block(level: int = 5) -> dict:
+    """Error against run time, the methodology of the paper's efficiency
+    tables, on the synthetic state: a 6 h integration on a level-5 grid from
+    the seeded balanced state (seed 2, 400 m), each scheme at dt in
+    {900, 1800, 3600} s and Tol in {1e-6, 1e-8, 1e-10}; error = relative L2 of
+    h at 6 h against exprb53 with dt = 225 s and Tol = 1e-12."""
+    import time
+    import torch
+    from paper_1805_02144_gb300.api import Grid, SchemeState, exprb_step
+    from paper_1805_02144_gb300.inputs import balanced_state
+    G = Grid(level)
+    ng = G.ncells
+    u0 = torch.from_numpy(balanced_state(G.cell_centres(), SEED, AMP)).cuda()
+    T = 6 * 3600.0
+
+    def run(scheme, dt, tol):
+        st = SchemeState(G)
+        u = u0
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(int(round(T / dt))):
+            u, info = exprb_step(G, scheme, dt, u, state=st, opts={"tol": tol}, stats=True)
+            if info["status"] != 0:
+                return None, info["status"], time.perf_counter() - t0
+        torch.cuda.synchronize()
+        return u, 0, time.perf_counter() - t0
+
+    ref, _, _ = run("exprb53", 225.0, 1e-12)
+    href = ref[3 * ng:]
+    rows = []
+    for scheme in ("exprb42", "pexprb43", "exprb53", "epi3"):
+        for dt in (900.0, 1800.0, 3600.0):
+            for tol in (1e-6, 1e-8, 1e-10):
+                u, st, wall = run(scheme, dt, tol)
+                err = None if u is None else float(torch.linalg.norm(u[3 * ng:] - href) / torch.linalg.norm(href))
+                rows.append({"scheme": scheme, "dt": dt, "tol": tol, "rel_err_h": err, "ms": 1e3 * wall,
+                             "status": st})
+    return {"workload": f"level-{level} grid ({ng} cells), 6 h from the seeded balanced state (seed 2, "
+                        "400 m), FP64; reference exprb53 dt 225 s Tol 1e-12; wall time per run with host "
+                        "status checks each step", "runs": rows}
+
+
 def conservation_block(level: int = 4, cap_s: float = 60.0) -> dict:
     """15 simulated days on a level-4 grid from the seeded balanced state
     (seed 2), FP64, Tol 1e-8, with the step sizes of the paper's conservation
@@ -571,6 +613,7 @@ def gpu_arm(args) -> None:
         line["adjoint"] = adjoint_block(flush)
         line["schemes"] = schemes_block(flush)
         line["conservation"] = conservation_block()
+        line["efficiency"] = efficiency_block()
     if world == 1 and not args.no_cpu_baseline:
         try:
             res = run_oracle_subprocess(1, 0)
@@ -605,7 +648,8 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the precision/batching/adjoint blocks")
-    ap.add_argument("--only", choices=["precision", "batching", "adjoint", "schemes", "conservation"],
+    ap.add_argument("--only", choices=["precision", "batching", "adjoint", "schemes", "conservation",
+                                       "efficiency"],
                     help="run one extra block alone and print it (for profiling)")
     args = ap.parse_args()
     if args.only:
@@ -615,7 +659,7 @@ def main():
         flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
         fn = {"precision": lambda: precision_block(flush), "batching": batching_block,
               "adjoint": lambda: adjoint_block(flush), "schemes": lambda: schemes_block(flush),
-              "conservation": conservation_block}[args.only]
+              "conservation": conservation_block, "efficiency": efficiency_block}[args.only]
         print(json.dumps({args.only: fn()}), flush=True)
         return
     if args.impl == "reference":
