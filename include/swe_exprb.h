@@ -55,7 +55,9 @@ typedef struct {
   int tol_mode;      /* 0: relative, Tol scaled by max_l ||v_l||_2; 1: absolute     */
   int m_init;        /* initial Krylov size (Algorithm 1: 1)                       */
   int m_max;         /* largest Krylov size, <= 64                                 */
-  int iom;           /* orthogonalisation window, must be 2 (IOM2)                 */
+  int iom;           /* orthogonalisation window: 2 (IOM2, the default) up to 64
+                        (full Arnoldi when >= m_max); exprb_step_adjoint and
+                        ensembles take 2 only                                      */
   double delta;      /* acceptance safety factor (Algorithm 1: 1.4)                */
   double gamma;      /* controller target for omega (0.8)                          */
   double kappa;      /* assumed error decrease per Krylov dimension (2)            */

@@ -136,6 +136,50 @@ __device__ bool grid_reduce(const A& a, SH& sh, double (&v)[K], int phase, Post 
   return sh.ok;
 }
 
+// Grid reduction of nv <= blockDim.x values whose block totals thread 0 of
+// every block has stored at partw[gb * WIDE_STRIDE + r].  Threads r < nv of
+// the block that arrives last each sum value r over blocks in block order
+// into ctrl->wide[r]; its thread 0 runs post(ctrl) and publishes; the other
+// blocks wait for the publication.
+template <class A, class SH, class Post>
+__device__ bool grid_reduce_wide(const A& a, SH& sh, int nv, int phase, Post post) {
+  __syncthreads();
+  GridSync* s = a.sync;
+  __shared__ unsigned int w_last, w_g0;
+  if (threadIdx.x == 0) {
+    w_g0 = *(volatile unsigned int*)&s->rgen;  // cannot advance before this block arrives
+    bool last;
+    flip_arrive(s, sh.gb, sh.gn, &last);
+    w_last = last ? 1u : 0u;
+    if (last) __threadfence();
+  }
+  __syncthreads();
+  if (w_last) {
+    if ((int)threadIdx.x < nv) {
+      double t = 0.0;
+      for (int b = 0; b < sh.gn; ++b) t += __ldcg(a.partw + (size_t)b * WIDE_STRIDE + threadIdx.x);
+      ((volatile double*)a.ctrl->wide)[threadIdx.x] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence_block();
+      post(make_volatile(a.ctrl));
+      __threadfence();
+      *(volatile unsigned int*)&s->rgen = w_g0 + 1;
+      sh.ok = ld_volatile_int(&s->abort) == 0;
+    }
+  } else if (threadIdx.x == 0) {
+    const volatile unsigned int* rg = &s->rgen;
+    const unsigned int g0 = w_g0;
+    const bool ok = bounded_spin(s, SWE_ERR_TIMEOUT, [&] { return *rg == g0; });
+    __threadfence();
+    sh.ok = ok && ld_volatile_int(&s->abort) == 0;
+  }
+  if (threadIdx.x == 0) phase_tick(a, sh, phase);
+  __syncthreads();
+  return sh.ok;
+}
+
 template <class A>
 __device__ __forceinline__ void abort_launch(const A& a, int code) {
   atomicCAS(&a.sync->abort, 0, code);

@@ -46,7 +46,13 @@ struct PhiCtrl {
   int wnz[PMAX + 1];
   int n_jv, n_sub, n_rej, m_last, m_max_used, status, replay_pos, attempts;
   int n_iter, n_wjv, comb_terms, pad;
+  // wider orthogonalisation windows (iom > 2): the dots of the last wide
+  // reduction and H[i][j] for i <= j - 2 (row-major, KMAX columns)
+  double wide[KMAX + 4];
+  double hup[KMAX * KMAX];
 };
+
+constexpr int WIDE_STRIDE = KMAX + 4;  // per-block stride of wide partial sums
 
 // Scalars of one accepted substep kept for the adjoint (tape mode).
 struct TapeSub {
@@ -85,6 +91,8 @@ struct PhiArgsT {
   R* tmp;                   // 8 x ng pass-1 planes (Laplacian 4, scalar/vector 4)
   R* Lring;                 // 3 x n: Laplacian planes of the last three raw slots
   R* Zbuf;                  // n: A v_j before orthogonalisation
+  R* Lbuf;                  // iom > 2: (KMAX + 1) x n Laplacian planes of every raw slot
+  double* partw;            // iom > 2: nblocks x WIDE_STRIDE partial dots
   double* part;             // NRED x nblocks partial sums (value-major)
   PhiCtrl* ctrl;
   GridSync* sync;
@@ -107,6 +115,7 @@ struct PhiArgsT {
   // options
   double tol, delta, gamma, kappa;
   int tol_mode, m_init, m_max, max_reject, max_substeps;
+  int iom;                  // orthogonalisation window (2: IOM2; up to KMAX: full)
   int64_t nA;
 };
 using PhiArgs = PhiArgsT<double>;

@@ -100,7 +100,16 @@ __device__ __forceinline__ int taylor_steps(double hnorm) {
 // ---------------------------------------------------------------------------
 constexpr int TAYLOR_TERMS = 32;
 
-__device__ void taylor_phi(Shared& sh, int m, int p, double tau, double hnorm) {
+// Entries of row r beyond the tridiagonal (iom > 2): sum over q = r+2 ..
+// min(m-1, r+iom-1) of tau H[r][q] x[q], in ascending q (empty for IOM2).
+__device__ __forceinline__ double hup_row(const double* hup, int iom, int r, int m, double tau, const double* x,
+                                          double v) {
+  const int qe = min(m - 1, r + iom - 1);
+  for (int q = r + 2; q <= qe; ++q) v = fma(tau * __ldcg(hup + r * KMAX + q), x[q], v);
+  return v;
+}
+
+__device__ void taylor_phi(Shared& sh, int m, int p, double tau, double hnorm, const double* hup, int iom) {
   const int r = threadIdx.x;
   const int M = m + p + 1;
   const int s = taylor_steps(hnorm);
@@ -127,6 +136,7 @@ __device__ void taylor_phi(Shared& sh, int m, int p, double tau, double hnorm) {
         v = cd * xc[r];
         if (r > 0) v = fma(cl, xc[r - 1], v);
         if (r < m - 1) v = fma(cu, xc[r + 1], v);
+        if (iom > 2) v = hup_row(hup, iom, r, m, tau, xc, v);
         if (r == 0) v += xc[m];
         v *= sh.ck[k];
       } else if (r < m + p) {
@@ -153,6 +163,7 @@ __device__ void taylor_phi(Shared& sh, int m, int p, double tau, double hnorm) {
     double v = cd * sh.x[r];
     if (r > 0) v = fma(cl, sh.x[r - 1], v);
     if (r < m - 1) v = fma(cu, sh.x[r + 1], v);
+    if (iom > 2) v = hup_row(hup, iom, r, m, tau, sh.x, v);
     if (r == 0) {
       double fact = 1.0;
       for (int k = 2; k <= p; ++k) fact *= k;
@@ -228,6 +239,9 @@ __device__ void decide(const A& a, Shared& sh) {
         double s = fabs(sh.hd[j]);
         if (j > 0) s += fabs(sh.hu[j - 1]);
         if (j + 1 < m_use) s += fabs(sh.hl[j + 1]);
+        if (a.iom > 2)
+          for (int i = max(0, j - a.iom + 1); i <= j - 2; ++i)
+            s += fabs(__ldcg((const double*)a.ctrl->hup + i * KMAX + j));
         cs = fmax(cs, s);
       }
 #pragma unroll
@@ -244,7 +258,7 @@ __device__ void decide(const A& a, Shared& sh) {
       return;
     }
     phase_tick(a, sh, PH_CONTROL);
-    taylor_phi(sh, m_use, p, tau_k, hnorm);
+    taylor_phi(sh, m_use, p, tau_k, hnorm, (const double*)a.ctrl->hup, a.iom);
     phase_tick(a, sh, PH_TAYLOR);
     hnext = (C->broken && m_use == C->size) ? 0.0 : sh.hl[m_use];
     eps = pow(tau_k, (double)p) * beta * tau_k * fabs(hnext) * fabs(sh.x[m_use - 1]);
@@ -388,6 +402,51 @@ template <>
 __device__ __forceinline__ double shared_coef<double>(const Shared& sh, int r) { return sh.coef[r]; }
 template <>
 __device__ __forceinline__ float shared_coef<float>(const Shared& sh, int r) { return sh.coeff[r]; }
+
+// Orthogonalisation of z = A v_j against the window of raw slots lo..lo+w-1
+// and pass 1 of the result at cell i (the form of orth_pass1_cell for
+// windows wider than two, iom > 2): z' = z - sum_r c_r raw_{lo+r} and, by
+// linearity, L z' = L z - sum_r c_r L raw_{lo+r} from the Laplacian planes
+// kept for every slot.  Returns |z'|^2 of the cell.
+template <typename R>
+__device__ __forceinline__ R orth_window_pass1_cell(const TablesT<R>& T, int i, const R* z, const SubBufs<R>& B,
+                                                    const R* Lbuf, int lo, int w, const Shared& sh, R* rnew,
+                                                    R* Lnew, const R* u, R* sq, size_t n, int p) {
+  const int ng = T.ng;
+  int nb[SLOTS];
+  load_nbr(T, i, nb);
+  R zp[4], nrm = R(0);
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const size_t e = (size_t)c * ng + i;
+    R v = ld(z + e);
+    R lz = lap_cell(T, i, nb, z + (size_t)c * ng);
+    for (int r = 0; r < w; ++r) {
+      const R cr = shared_coef<R>(sh, r);
+      v = fma(-cr, ld(B.raw(lo + r, n, p) + e), v);
+      lz = fma(-cr, ld(Lbuf + (size_t)(lo + r) * n + e), lz);
+    }
+    zp[c] = v;
+    rnew[e] = v;
+    Lnew[e] = lz;
+    nrm = fma(v, v, nrm);
+  }
+  R uv[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) uv[c] = ld(u + (size_t)c * ng + i);
+  sq[i] = fma(uv[0], zp[0], fma(uv[1], zp[1], fma(uv[2], zp[2], T.g * zp[3])));
+#pragma unroll
+  for (int c = 0; c < 3; ++c) sq[(size_t)(1 + c) * ng + i] = fma(zp[c], uv[3], uv[c] * zp[3]);
+  return nrm;
+}
+
+// H[i][j] of the control block for any i <= j + 1.
+__device__ __forceinline__ double h_entry(volatile PhiCtrl* c, int i, int j) {
+  if (i == j + 1) return c->hl[j + 1];
+  if (i == j) return c->hd[j];
+  if (i == j - 1) return c->hu[j - 1];
+  return c->hup[i * KMAX + j];
+}
 
 // Algorithm 1 for one call, executed by the sh.gn blocks of a group.  Returns
 // false when the launch is being aborted (every block of the group returns
@@ -563,6 +622,90 @@ __device__ bool phi_run(const PhiArgsT<R>& a, Shared& sh) {
           // by one grid reduction.  Pass-1 planes of raw slot j: Laplacian in
           // Lring[j % 3], scalar/vector planes in SQ.
           R* SQ = a.tmp + (size_t)4 * ng;
+          // windows wider than two (iom > 2, up to full orthogonalisation):
+          // the same three phases with w window dots in one wide reduction
+          while (a.iom > 2 && vldi(&C->size) < m_req && !vldi(&C->broken)) {
+            const int j = vldi(&C->size);
+            const int lo = max(0, j - a.iom + 1), w = j - lo + 1;
+            R* rj = B.raw(j, n, p);
+            R* rj1 = B.raw(j + 1, n, p);
+            R* Lj = a.Lbuf + (size_t)j * n;
+            R* Lj1 = a.Lbuf + (size_t)(j + 1) * n;
+            const double sj = vld(&C->sig[j]);
+            if (j == 0) {
+              FOR_CELLS(i)
+                pass1_cell<MODE_J>(T, i, rj, R(1), a.u_lin, Lj, SQ);
+              if (!grid_barrier(a, sh, PH_K_PASS1)) return false;
+            }
+            const R zs = (R)(a.dt * sj);
+            FOR_CELLS(i) {
+              R o[4];
+              pass2_cell<MODE_J>(T, i, rj, R(1), Lj, SQ, a.aux, o);
+#pragma unroll
+              for (int c = 0; c < 4; ++c) a.Zbuf[(size_t)c * ng + i] = zs * o[c];
+            }
+            for (int r = 0; r < w; ++r) {  // window dots <z, raw_{lo+r}>, block sums in order
+              const R* rr = B.raw(lo + r, n, p);
+              R acc = R(0);
+              FOR_CELLS(i)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                  const size_t e = (size_t)c * ng + i;
+                  acc = fma(a.Zbuf[e], ld(rr + e), acc);
+                }
+              double v1[1] = {(double)acc};
+              block_sum<1>(v1, sh.red);
+              if (threadIdx.x == 0) a.partw[(size_t)sh.gb * WIDE_STRIDE + r] = v1[0];
+            }
+            auto post_wdots = [j, lo, w](volatile PhiCtrl* c) {
+              for (int r = 0; r < w; ++r) {
+                const int i = lo + r;
+                const double h = c->sig[i] * c->wide[r];
+                if (i == j)
+                  c->hd[j] = h;
+                else if (i == j - 1)
+                  c->hu[j - 1] = h;
+                else
+                  c->hup[i * KMAX + j] = h;
+              }
+            };
+            if (!grid_reduce_wide(a, sh, w, PH_K_PASS2, post_wdots)) return false;
+            for (int r = threadIdx.x; r < w; r += blockDim.x) {
+              const int i = lo + r;
+              sh.coef[r] = h_entry(C, i, j) * vld(&C->sig[i]);
+              sh.coeff[r] = (float)sh.coef[r];
+            }
+            __syncthreads();
+            R nrm = R(0);
+            FOR_CELLS(i)
+              nrm += orth_window_pass1_cell(T, i, a.Zbuf, B, a.Lbuf, lo, w, sh, rj1, Lj1, a.u_lin, SQ, n, p);
+            double wn[1] = {(double)nrm};
+            GridSync* gs = a.sync;
+            auto post_wnorm = [gs, j, lo, w, bd](volatile PhiCtrl* c, bool leader) {
+              double hn = sqrt((double)c->red[0]);
+              double ref = 0.0;
+              for (int r = 0; r < w; ++r) ref += fabs(h_entry(c, lo + r, j));
+              c->size = j + 1;
+              if (leader) {
+                c->n_jv += 1;
+                c->n_iter += 1;
+              }
+              if (!isfinite(hn) || !isfinite(ref)) {
+                c->status = SWE_ERR_NONFINITE;
+                atomicCAS(&gs->abort, 0, SWE_ERR_NONFINITE);
+                return;
+              }
+              if (hn <= bd * ref) {  // happy breakdown: invariant subspace
+                c->broken = 1;
+                c->hl[j + 1] = 0.0;
+                c->sig[j + 1] = 0.0;
+              } else {
+                c->hl[j + 1] = hn;
+                c->sig[j + 1] = 1.0 / hn;
+              }
+            };
+            if (!grid_reduce<1>(a, sh, wn, PH_ORTH, post_wnorm)) return false;
+          }
           while (vldi(&C->size) < m_req && !vldi(&C->broken)) {
             const int j = vldi(&C->size);
             R* rj = B.raw(j, n, p);

@@ -107,6 +107,10 @@ struct swe_grid {
   cudaEvent_t stage_ev = nullptr;
   int* adj_status = nullptr;    // device: first error of the adjoint launches of a step
   double* dhs = nullptr;        // surface height h_s (device), when set
+  // windows wider than two (iom > 2): Laplacian planes of every basis slot
+  // and wide partial sums, per precision, created on first use
+  void* dwide = nullptr;
+  void* dwideF = nullptr;
 };
 
 struct swe_ensemble {
@@ -496,11 +500,12 @@ int resolve_opts(const phi_opts* in, phi_opts& o) {
     o = *in;
   else
     swe_phi_opts_default(&o);
-  if (!(o.tol > 0.0) || o.m_init < 1 || o.m_max < 1 || o.m_max > KMAX || o.iom != 2 ||
+  if (!(o.tol > 0.0) || o.m_init < 1 || o.m_max < 1 || o.m_max > KMAX ||
       !(o.delta > 0.0) || !(o.gamma > 0.0) || !(o.kappa > 1.0) || o.max_reject < 0 || o.max_substeps < 1 ||
+      o.iom < 2 || o.iom > KMAX ||
       (o.tol_mode != 0 && o.tol_mode != 1) || (o.replay && o.n_replay < 1) ||
       (o.precision != 0 && o.precision != 1))
-    return fail(SWE_ERR_INVALID_ARG, "invalid phi_opts (m_max <= 64, iom == 2, tol > 0, kappa > 1)");
+    return fail(SWE_ERR_INVALID_ARG, "invalid phi_opts (m_max <= 64, 2 <= iom <= 64, tol > 0, kappa > 1)");
   return SWE_OK;
 }
 
@@ -568,6 +573,7 @@ void fill_phi_args(swe_grid* g, A& a, double dt, int p, int ns, const double* rh
   a.m_max = o.m_max;
   a.max_reject = o.max_reject;
   a.max_substeps = o.max_substeps;
+  a.iom = o.iom;
   a.nA = g->host.nA;
   a.prof = g->prof_on ? g->dprof : nullptr;
 }
@@ -591,6 +597,27 @@ int prepare_lin(swe_grid* g, const double* u_lin, const phi_opts& o, cudaStream_
 }
 
 // One phipm_simul_iom2 evaluation; prepare_lin(u_lin) must precede it on the stream.
+// Buffers of the wide-window path (iom > 2) for precision R: (KMAX + 1)
+// Laplacian planes and nblocks x WIDE_STRIDE partial sums.
+template <typename R>
+int ensure_wide(swe_grid* g, R** Lbuf, double** partw) {
+  void*& mem = sizeof(R) == 8 ? g->dwide : g->dwideF;
+  const PhiLaunch& L = sizeof(R) == 8 ? g->launch : g->launchF;
+  const size_t n = (size_t)4 * g->T.ng;
+  const size_t lbytes = ((size_t)(KMAX + 1) * n * sizeof(R) + 255) & ~size_t(255);
+  if (!mem) {
+    const size_t total = lbytes + (size_t)L.nblocks * WIDE_STRIDE * sizeof(double);
+    cudaError_t e = cudaMalloc(&mem, total);
+    if (e != cudaSuccess) {
+      mem = nullptr;
+      return fail(SWE_ERR_NOMEM, std::string("wide-window buffers: ") + cudaGetErrorString(e));
+    }
+  }
+  *Lbuf = (R*)mem;
+  *partw = (double*)((char*)mem + lbytes);
+  return SWE_OK;
+}
+
 // Tape of one recorded call (device pointers inside swe_grid::dtape).
 struct TapeCall {
   double* W = nullptr;
@@ -618,6 +645,10 @@ int phi_call(swe_grid* g, const double* u_lin, double dt, int p, const double* c
     a.Lring = g->Lring;
     a.Zbuf = g->Zbuf;
     fill_phi_args(g, a, dt, p, ns, rho, o, call_index, m_slot, replay_offset);
+    if (o.iom > 2) {
+      int rc = ensure_wide<double>(g, &a.Lbuf, &a.partw);
+      if (rc) return rc;
+    }
     if (tape) {
       a.tapeW = tape->W;
       a.tapeV = tape->V;
@@ -654,6 +685,10 @@ int phi_call(swe_grid* g, const double* u_lin, double dt, int p, const double* c
   a.Lring = g->LringF;
   a.Zbuf = g->ZbufF;
   fill_phi_args(g, a, dt, p, ns, rho, o, call_index, m_slot, replay_offset);
+  if (o.iom > 2) {
+    int rc = ensure_wide<float>(g, &a.Lbuf, &a.partw);
+    if (rc) return rc;
+  }
   ProfSpan span(g, st, &g->phi_ev);
   int e = launch_phi_kernel(g->launchF, a, st);
   if (e != 0) return cuda_fail((cudaError_t)e, "cudaLaunchCooperativeKernel(phi_kernel<float>)");
@@ -1037,6 +1072,8 @@ void swe_destroy_grid(swe_grid* g) {
   if (g->hstage) cudaFreeHost(g->hstage);
   if (g->stage_ev) cudaEventDestroy(g->stage_ev);
   if (g->dhs) cudaFree(g->dhs);
+  if (g->dwide) cudaFree(g->dwide);
+  if (g->dwideF) cudaFree(g->dwideF);
   delete g;
 }
 
@@ -1346,6 +1383,7 @@ int exprb_step_adjoint(swe_grid* g, int scheme, double dt, const double* u_n, co
   phi_opts o;
   if ((rc = resolve_opts(opts, o))) return rc;
   if (o.precision != 0) return fail(SWE_ERR_INVALID_ARG, "exprb_step_adjoint: FP64 only (precision = 0)");
+  if (o.iom != 2) return fail(SWE_ERR_INVALID_ARG, "exprb_step_adjoint: IOM2 only (iom = 2)");
   if ((rc = ensure_workspace(g))) return rc;
   if ((rc = ensure_adjoint(g))) return rc;
   cudaStream_t st = S(stream);
@@ -1624,7 +1662,8 @@ extern "C" int swe_ensemble_create(swe_grid* const* grids, int nmem, const doubl
   phi_opts o;
   int rc = resolve_opts(opts, o);
   if (rc) return rc;
-  if (o.precision != 0 || o.replay) return fail(SWE_ERR_INVALID_ARG, "ensemble: FP64 without replay only");
+  if (o.precision != 0 || o.replay || o.iom != 2)
+    return fail(SWE_ERR_INVALID_ARG, "ensemble: FP64, IOM2, without replay only");
   int NB = 0, threads = 0;
   if (ens_max_blocks(&NB, &threads) != 0) return fail(SWE_ERR_CUDA, "ensemble: occupancy query failed");
   if (nmem > NB) return fail(SWE_ERR_INVALID_ARG, "ensemble: more members than co-resident blocks");
@@ -1735,6 +1774,7 @@ extern "C" int swe_ensemble_create(swe_grid* const* grids, int nmem, const doubl
       a.m_max = o.m_max;
       a.max_reject = o.max_reject;
       a.max_substeps = o.max_substeps;
+      a.iom = 2;
       a.nA = g->host.nA;
     }
     M.c1.p = 1;
