@@ -260,24 +260,34 @@ __device__ void decide(const A& a, Shared& sh) {
     phase_tick(a, sh, PH_CONTROL);
     taylor_phi(sh, m_use, p, tau_k, hnorm, (const double*)a.ctrl->hup, a.iom);
     phase_tick(a, sh, PH_TAYLOR);
-    hnext = (C->broken && m_use == C->size) ? 0.0 : sh.hl[m_use];
-    eps = pow(tau_k, (double)p) * beta * tau_k * fabs(hnext) * fabs(sh.x[m_use - 1]);
   }
+  // The rest is scalar work: warp 0 alone, its lanes evaluating the powers and
+  // the two costs side by side (the other warps wait at the next barrier).
+  if (lane >= 32) return;
+  constexpr unsigned FULL = 0xffffffffu;
+  const double pw = pow(tau_k, (double)min(lane, p));  // lane j <= p: tau_k^j
+  const double tp = __shfl_sync(FULL, pw, p);
+  if (beta > 0.0) {
+    hnext = (C->broken && m_use == C->size) ? 0.0 : sh.hl[m_use];
+    eps = tp * beta * tau_k * fabs(hnext) * fabs(sh.x[m_use - 1]);
+  }
+  double tpow[PMAX];
+#pragma unroll
+  for (int j = 0; j < PMAX; ++j) tpow[j] = __shfl_sync(FULL, pw, min(j, p));
   const double omega = t_out * eps / (tau_k * a.tol * C->scale);
   const bool accepted = replay ? (rec_acc != 0) : (omega <= a.delta);
 
-  // combination coefficients (all lanes, then lane 0 finishes the scalars)
+  // combination coefficients (warp 0, then lane 0 finishes the scalars)
   if (accepted) {
-    const double tp = pow(tau_k, (double)p);
     if (beta > 0.0) {
-      for (int r = lane; r < m_use; r += blockDim.x) C->cV[r] = tp * beta * sh.y[r] * C->sig[r];
+      for (int r = lane; r < m_use; r += 32) C->cV[r] = tp * beta * sh.y[r] * C->sig[r];
       if (lane == 0)
         C->cV[m_use] = hnext != 0.0 ? tp * beta * tau_k * hnext * sh.x[m_use - 1] * C->sig[m_use] : 0.0;
     }
     if (a.tape_sub) {  // keep what the adjoint needs of this substep
       TapeSub& S = a.tape_sub[C->n_sub];
       if (beta > 0.0)
-        for (int r = lane; r <= m_use; r += blockDim.x) {
+        for (int r = lane; r <= m_use; r += 32) {
           S.sig[r] = C->sig[r];
           S.hd[r] = sh.hd[r];
           S.hu[r] = sh.hu[r];
@@ -297,13 +307,14 @@ __device__ void decide(const A& a, Shared& sh) {
       }
     }
   }
-  __syncthreads();
-  if (lane != 0) return;
+  __syncwarp();
 
   // proposals (reading R8 of the oracle, the same arithmetic)
   if (!isfinite(omega)) {
-    C->status = SWE_ERR_NONFINITE;
-    abort_launch(a, SWE_ERR_NONFINITE);
+    if (lane == 0) {
+      C->status = SWE_ERR_NONFINITE;
+      abort_launch(a, SWE_ERR_NONFINITE);
+    }
     return;
   }
   const int cap = C->broken ? C->size : a.m_max;
@@ -313,10 +324,13 @@ __device__ void decide(const A& a, Shared& sh) {
     tau_new = 2.0 * tau_k;
     m_new = max(1, (3 * m_use + 3) / 4);
   } else {
-    double q = fmax(1.0, m_use / 4.0);
-    tau_new = tau_k * pow(omega / a.gamma, -1.0 / q);
+    // lane 0: the step-size factor, lane 1: the Krylov-size increment
+    double f = 0.0;
+    if (lane == 0) f = pow(omega / a.gamma, -1.0 / fmax(1.0, m_use / 4.0));
+    if (lane == 1) f = ceil(log(omega / a.gamma) / log(a.kappa));
+    tau_new = tau_k * __shfl_sync(FULL, f, 0);
     tau_new = fmin(fmax(tau_new, tau_k / 5.0), 2.0 * tau_k);
-    int dm = (int)ceil(log(omega / a.gamma) / log(a.kappa));
+    const int dm = (int)__shfl_sync(FULL, f, 1);
     m_new = m_use + dm;
     m_new = min(max(m_new, (3 * m_use + 3) / 4), (m_use * 4) / 3 + 1);
   }
@@ -327,8 +341,12 @@ __device__ void decide(const A& a, Shared& sh) {
     // ||tau_new Hhat||_1 = max(tau_new * max column sum of |H_m|, 1)
     hnorm_new = fmax(tau_new * sh.scal[0], 1.0);
   }
-  const double c_tau = cost_fn(tau_new, m_use, p, remaining, N, nA, hnorm_new);
-  const double c_m = cost_fn(tau_k, m_new, p, remaining, N, nA, hnorm);
+  // lane 0: C(tau_new, m), lane 1: C(tau, m_new), evaluated side by side
+  const double c_lane = cost_fn(lane == 0 ? tau_new : tau_k, lane == 0 ? m_use : m_new, p, remaining, N, nA,
+                                lane == 0 ? hnorm_new : hnorm);
+  const double c_tau = __shfl_sync(FULL, c_lane, 0);
+  const double c_m = __shfl_sync(FULL, c_lane, 1);
+  if (lane != 0) return;
   const bool take_tau = (c_tau <= c_m) || (!accepted && m_new == m_use);
 
   // trace
@@ -357,7 +375,7 @@ __device__ void decide(const A& a, Shared& sh) {
     double f = 1.0;
     for (int j = 0; j < p; ++j) {
       if (j > 0) f *= (double)j;
-      C->cW[j] = pow(tau_k, (double)j) / f;
+      C->cW[j] = tpow[j] / f;
     }
     C->ncomb = beta > 0.0 ? m_use + 1 : 0;
     C->comb_terms += C->ncomb + p;
