@@ -600,16 +600,15 @@ __device__ bool adj_run(const AdjArgs& a, AdjShared& sh) {
           }
         }
         const TapeSub* Sp = &S;
-        auto post = [Sp, j](volatile AdjCtrl* c, bool) {
+        auto post = [Sp, j](volatile AdjCtrl* c, bool, const auto& r) {
           volatile AdjCtrl* cc2 = c;
           const TapeSub& St = *Sp;
           if (j >= 1) {
             const int jn = j - 1;  // next column: Vb_{jn+1} = Vbar_j
             const double sj = St.sig[j], sm = St.sig[j - 1], s2 = j >= 2 ? St.sig[j - 2] : 0.0;
-            adj_column_scalars(cc2, St, jn, sj * c->red[0], s2 * c->red[1], sj * s2 * c->red[2],
-                               sm * c->red[3], sj * sm * c->red[4]);
+            adj_column_scalars(cc2, St, jn, sj * r[0], s2 * r[1], sj * s2 * r[2], sm * r[3], sj * sm * r[4]);
           } else {
-            cc2->col[3] = St.sig[0] * c->red[0];  // <Vbar_0, v_0>
+            cc2->col[3] = St.sig[0] * r[0];  // <Vbar_0, v_0>
           }
         };
         if (!grid_reduce<5>(a, sh, d, AP_C, post)) return false;

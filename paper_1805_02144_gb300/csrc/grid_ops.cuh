@@ -85,8 +85,16 @@ __device__ bool grid_barrier(const A& a, SH& sh, int phase) {
 // at part[k * gn + b]); warp 0 of the block that arrives last sums them over
 // blocks (lane l takes blocks l, l+32, ..., then a fixed shuffle tree, so the
 // result is bitwise reproducible), stores them in ctrl->red[], runs
-// post(ctrl, true) on its lane 0 and publishes; the other blocks wait for
-// the publication.
+// post(ctrl, true, sums) on its lane 0 (the sums passed in registers, so the
+// post reads nothing back over the bus) and publishes; the other blocks wait
+// for the publication.
+// The K sums of a grid reduction, handed to the post function by value.
+template <int K>
+struct RedSums {
+  double v[K];
+  __device__ __forceinline__ double operator[](int k) const { return v[k]; }
+};
+
 template <int K, class A, class SH, class Post>
 __device__ bool grid_reduce(const A& a, SH& sh, double (&v)[K], int phase, Post post) {
   static_assert(K <= NRED, "reduction width");
@@ -109,6 +117,10 @@ __device__ bool grid_reduce(const A& a, SH& sh, double (&v)[K], int phase, Post 
       double t[K];
 #pragma unroll
       for (int k = 0; k < K; ++k) t[k] = 0.0;
+      // unrolled so that a lane's loads are in flight together, about eight
+      // values at a time (the sum order over b is unchanged)
+      constexpr int kUnroll = K >= 8 ? 1 : (K >= 4 ? 2 : 8 / K);
+#pragma unroll kUnroll
       for (int b = threadIdx.x; b < gn; b += 32)
 #pragma unroll
         for (int k = 0; k < K; ++k) t[k] += __ldcg(a.part + (size_t)k * gn + b);
@@ -118,8 +130,13 @@ __device__ bool grid_reduce(const A& a, SH& sh, double (&v)[K], int phase, Post 
         for (int o = 16; o > 0; o >>= 1) t[k] += __shfl_down_sync(0xffffffffu, t[k], o);
       if (threadIdx.x == 0) {
         auto* vc = make_volatile(a.ctrl);
-        for (int k = 0; k < K; ++k) vc->red[k] = t[k];
-        post(vc, true);
+        RedSums<K> r;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+          vc->red[k] = t[k];
+          r.v[k] = t[k];
+        }
+        post(vc, true, r);
         __threadfence();
         *(volatile unsigned int*)&s->rgen = g0 + 1;
         sh.ok = ld_volatile_int(&s->abort) == 0;

@@ -520,12 +520,14 @@ __device__ bool phi_run(const PhiArgsT<R>& a, Shared& sh) {
     const int pp = p, tol_mode = a.tol_mode, m_max = a.m_max;
     const double rho0 = a.rho[0];
     const int m_init = (a.m_slot && *a.m_slot > 0) ? *a.m_slot : a.m_init;
-    auto post = [pp, tol_mode, m_max, rho0, m_init](volatile PhiCtrl* c, bool) {
+    auto post = [pp, tol_mode, m_max, rho0, m_init](volatile PhiCtrl* c, bool, const auto& r) {
       double mx = 0.0;
-      for (int l = 0; l <= pp; ++l) mx = fmax(mx, (double)c->red[1 + l]);
+#pragma unroll
+      for (int l = 0; l <= PMAX; ++l)
+        if (l <= pp) mx = fmax(mx, r[1 + l]);
       double scale = tol_mode == 0 ? sqrt(mx) : 1.0;
       c->scale = scale;
-      c->wnz[0] = c->red[0] > 0.0;
+      c->wnz[0] = r[0] > 0.0;
       c->t = 0.0;
       c->tau = rho0;
       c->m = max(1, min(m_init, m_max));
@@ -601,14 +603,14 @@ __device__ bool phi_run(const PhiArgsT<R>& a, Shared& sh) {
         }
         double v[2] = {(double)nzc, (double)sqs};
         GridSync* gs = a.sync;
-        auto post = [gs, j, nz_prev, p](volatile PhiCtrl* c, bool leader) {
-          c->wnz[j] = c->red[0] > 0.0;
+        auto post = [gs, j, nz_prev, p](volatile PhiCtrl* c, bool leader, const auto& r) {
+          c->wnz[j] = r[0] > 0.0;
           if (nz_prev && leader) {
             c->n_jv += 1;
             c->n_wjv += 1;
           }
           if (j == p) {
-            double b = sqrt((double)c->red[1]);
+            double b = sqrt(r[1]);
             c->beta = b;
             c->sig[0] = b > 0.0 ? 1.0 / b : 0.0;
             c->size = 0;
@@ -699,8 +701,8 @@ __device__ bool phi_run(const PhiArgsT<R>& a, Shared& sh) {
               nrm += orth_window_pass1_cell(T, i, a.Zbuf, B, a.Lbuf, lo, w, sh, rj1, Lj1, a.u_lin, SQ, n, p);
             double wn[1] = {(double)nrm};
             GridSync* gs = a.sync;
-            auto post_wnorm = [gs, j, lo, w, bd](volatile PhiCtrl* c, bool leader) {
-              double hn = sqrt((double)c->red[0]);
+            auto post_wnorm = [gs, j, lo, w, bd](volatile PhiCtrl* c, bool leader, const auto& r) {
+              double hn = sqrt(r[0]);
               double ref = 0.0;
               for (int r = 0; r < w; ++r) ref += fabs(h_entry(c, lo + r, j));
               c->size = j + 1;
@@ -733,6 +735,7 @@ __device__ bool phi_run(const PhiArgsT<R>& a, Shared& sh) {
             R* Ljm = a.Lring + (size_t)((j + 2) % 3) * n;
             R* Lj1 = a.Lring + (size_t)((j + 1) % 3) * n;
             const double sj = vld(&C->sig[j]);
+            const double sjm = j > 0 ? vld(&C->sig[j - 1]) : 0.0;
             if (j == 0) {
               FOR_CELLS(i)
                 pass1_cell<MODE_J>(T, i, rj, R(1), a.u_lin, Lj, SQ);
@@ -753,22 +756,24 @@ __device__ bool phi_run(const PhiArgsT<R>& a, Shared& sh) {
               }
             }
             double v[2] = {(double)d0, (double)d1};
-            auto post_dots = [j](volatile PhiCtrl* c, bool) {
-              if (j > 0) c->hu[j - 1] = c->sig[j - 1] * c->red[0];
-              c->hd[j] = c->sig[j] * c->red[1];
+            auto post_dots = [j, sj, sjm](volatile PhiCtrl* c, bool, const auto& r) {
+              if (j > 0) c->hu[j - 1] = sjm * r[0];
+              c->hd[j] = sj * r[1];
             };
             if (!grid_reduce<2>(a, sh, v, PH_K_PASS2, post_dots)) return false;
             // z' = z - h_{j-1,j} v_{j-1} - h_{j,j} v_j with its pass-1 planes
-            const R am = j > 0 ? (R)(vld(&C->hu[j - 1]) * vld(&C->sig[j - 1])) : R(0);
-            const R aj = (R)(vld(&C->hd[j]) * sj);
+            const double hdj = vld(&C->hd[j]);
+            const double huj = j > 0 ? vld(&C->hu[j - 1]) : 0.0;
+            const R am = j > 0 ? (R)(huj * sjm) : R(0);
+            const R aj = (R)(hdj * sj);
             R nrm = R(0);
             FOR_CELLS(i)
               nrm += orth_pass1_cell(T, i, a.Zbuf, rj, rjm, aj, am, Lj, Ljm, rj1, Lj1, a.u_lin, SQ);
             double w[1] = {(double)nrm};
             GridSync* gs = a.sync;
-            auto post_norm = [gs, j, bd](volatile PhiCtrl* c, bool leader) {
-              double hn = sqrt((double)c->red[0]);
-              double ref = fabs((double)c->hd[j]) + (j > 0 ? fabs((double)c->hu[j - 1]) : 0.0);
+            auto post_norm = [gs, j, bd, hdj, huj](volatile PhiCtrl* c, bool leader, const auto& r) {
+              double hn = sqrt(r[0]);
+              double ref = fabs(hdj) + (j > 0 ? fabs(huj) : 0.0);
               c->size = j + 1;
               if (leader) {
                 c->n_jv += 1;
@@ -823,7 +828,7 @@ __device__ bool phi_run(const PhiArgsT<R>& a, Shared& sh) {
           }
         }
         double v[1] = {(double)nzy};
-        auto post_y = [](volatile PhiCtrl* c, bool) { c->wnz[0] = c->red[0] > 0.0; };
+        auto post_y = [](volatile PhiCtrl* c, bool, const auto& r) { c->wnz[0] = r[0] > 0.0; };
         if (!grid_reduce<1>(a, sh, v, PH_COMBINE, post_y)) return false;
         break;
       }
