@@ -105,8 +105,8 @@ def run_oracle_subprocess(nsteps: int, warmup: int, threads: int = 1) -> dict:
 
 
 def reference_arm(args) -> None:
-    rank = int(os.environ.get("RANK", "0"))
-    if rank != 0:
+    from paper_1805_02144_gb300.ranks import from_env
+    if not from_env().lead:  # the oracle runs once, on rank 0
         return
     res = run_oracle_subprocess(args.steps, min(args.warmup, 1))
     total = sum(res["times"])
@@ -507,9 +507,9 @@ def adjoint_block(flush) -> dict:
 
 def gpu_arm(args) -> None:
     import torch
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_1805_02144_gb300.ranks import from_env, job_rate, max_over_ranks
+    rk = from_env()
+    world, rank, local = rk.world, rk.rank, rk.local
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
@@ -536,12 +536,8 @@ def gpu_arm(args) -> None:
     if dist:
         dist.barrier()
     clocks = sampler.stop()
-    t_ms = sum(ms)
-    if dist:
-        t = torch.tensor([t_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_ms = float(t.item())
-    value = world * args.steps / (t_ms / 1e3)
+    t_ms = max_over_ranks(sum(ms), dist, "cuda")
+    value = job_rate(world, args.steps, t_ms)
 
     # end to end through the public API: pinned host state in, host state out
     n = G.n
@@ -564,12 +560,8 @@ def gpu_arm(args) -> None:
         ev2[k][1].synchronize()
         h_in, h_out = h_out, h_in
     torch.cuda.synchronize()
-    e_ms = sum(a.elapsed_time(b) for a, b in ev2)
-    if dist:
-        t = torch.tensor([e_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e_ms = float(t.item())
-    e2e = world * args.steps / (e_ms / 1e3)
+    e_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev2), dist, "cuda")
+    e2e = job_rate(world, args.steps, e_ms)
     finite = bool(torch.isfinite(ucur).all().item())
 
     if rank != 0:
