@@ -815,16 +815,49 @@ __device__ bool phi_run(const PhiArgsT<R>& a, Shared& sh) {
         const bool land = vldi(&C->land) != 0;
         R* yo = land ? a.y_out[oi] : nullptr;
         int nzy = 0;
+        // Per element the sum runs over w_0..w_{p-1}, then raw slots 0..ncomb-1,
+        // one FMA each in that order; a thread loads four slots x four
+        // components of its cell before it uses them, so that enough loads are
+        // in flight to cover the memory latency.
         FOR_CELLS(i) {
+          R y[4] = {R(0), R(0), R(0), R(0)};
+          for (int j = 0; j < p; ++j) {
+            const R cj = shared_coef<R>(sh, KMAX + 2 + j);
+            const R* src = B.Wk + (size_t)j * n + i;
+            R wv[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) wv[c] = src[(size_t)c * ng];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) y[c] = fma(cj, wv[c], y[c]);
+          }
+          int r = 0;
+          for (; r + 4 <= ncomb; r += 4) {
+            R xv[4][4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const R* src = B.raw(r + q, n, p) + i;
+#pragma unroll
+              for (int c = 0; c < 4; ++c) xv[q][c] = src[(size_t)c * ng];
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const R cq = shared_coef<R>(sh, r + q);
+#pragma unroll
+              for (int c = 0; c < 4; ++c) y[c] = fma(cq, xv[q][c], y[c]);
+            }
+          }
+          for (; r < ncomb; ++r) {
+            const R cr = shared_coef<R>(sh, r);
+            const R* src = B.raw(r, n, p) + i;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) y[c] = fma(cr, src[(size_t)c * ng], y[c]);
+          }
 #pragma unroll
           for (int c = 0; c < 4; ++c) {
             const size_t e = (size_t)c * ng + i;
-            R y = R(0);
-            for (int j = 0; j < p; ++j) y = fma(shared_coef<R>(sh, KMAX + 2 + j), B.Wk[(size_t)j * n + e], y);
-            for (int r = 0; r < ncomb; ++r) y = fma(shared_coef<R>(sh, r), B.raw(r, n, p)[e], y);
-            B.Wnext[e] = y;
-            if (yo) yo[e] = y;
-            nzy += (y != R(0)) ? 1 : 0;
+            B.Wnext[e] = y[c];
+            if (yo) yo[e] = y[c];
+            nzy += (y[c] != R(0)) ? 1 : 0;
           }
         }
         double v[1] = {(double)nzy};
