@@ -816,9 +816,11 @@ __device__ bool phi_run(const PhiArgsT<R>& a, Shared& sh) {
         R* yo = land ? a.y_out[oi] : nullptr;
         int nzy = 0;
         // Per element the sum runs over w_0..w_{p-1}, then raw slots 0..ncomb-1,
-        // one FMA each in that order; a thread loads four slots x four
+        // one FMA each in that order; a thread loads kQ slots x four
         // components of its cell before it uses them, so that enough loads are
-        // in flight to cover the memory latency.
+        // in flight to cover the memory latency (kQ = 4 within the FP32
+        // kernel's 64 registers).
+        constexpr int kQ = sizeof(R) == 8 ? 8 : 4;
         FOR_CELLS(i) {
           R y[4] = {R(0), R(0), R(0), R(0)};
           for (int j = 0; j < p; ++j) {
@@ -831,16 +833,16 @@ __device__ bool phi_run(const PhiArgsT<R>& a, Shared& sh) {
             for (int c = 0; c < 4; ++c) y[c] = fma(cj, wv[c], y[c]);
           }
           int r = 0;
-          for (; r + 4 <= ncomb; r += 4) {
-            R xv[4][4];
+          for (; r + kQ <= ncomb; r += kQ) {
+            R xv[kQ][4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
+            for (int q = 0; q < kQ; ++q) {
               const R* src = B.raw(r + q, n, p) + i;
 #pragma unroll
               for (int c = 0; c < 4; ++c) xv[q][c] = src[(size_t)c * ng];
             }
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
+            for (int q = 0; q < kQ; ++q) {
               const R cq = shared_coef<R>(sh, r + q);
 #pragma unroll
               for (int c = 0; c < 4; ++c) y[c] = fma(cq, xv[q][c], y[c]);

@@ -128,3 +128,49 @@ def test_rejects_bad_rho_and_reports_no_convergence():
         phipm_simul_iom2(Amul, [0.9, 0.5], v, PhiOpts(), s.nA)
     with pytest.raises(NoConvergence):
         phipm_simul_iom2(Amul, [1.0], v, PhiOpts(tol=1e-30, max_reject=3, m_max=4), s.nA)
+
+
+# --- wider orthogonalisation windows (iom > 2, full Arnoldi at iom >= m) -----
+def test_full_arnoldi_basis_is_orthonormal_and_satisfies_the_arnoldi_relation():
+    """iom >= m: V_m orthonormal, H_m upper Hessenberg, A V_m = V_{m+1} Hbar_m."""
+    from oracle.phipm import IOM2Basis
+    s, u, A, Amul = _setup()
+    v1 = random_vector(s.n, 5)
+    v1 /= np.linalg.norm(v1)
+    m = 20
+    B = IOM2Basis(lambda x: A @ x, v1, iom=64, m_max=m, bd=1e-13)
+    assert B.extend(m) == m
+    V = np.stack(B.V[:m + 1], axis=1)
+    assert np.abs(V.T @ V - np.eye(m + 1)).max() <= 1e-10
+    H = B.H[:m + 1, :m]
+    assert np.all(np.tril(H, -2) == 0.0)                       # upper Hessenberg
+    assert np.linalg.norm(A @ V[:, :m] - V @ H) <= 1e-12 * np.linalg.norm(A @ V[:, :m])
+
+
+def test_symmetric_matrix_gives_the_same_tridiagonal_h_for_any_window():
+    """For symmetric A, Arnoldi reduces to Lanczos: the full-window H equals the
+    IOM2 H (tridiagonal), up to rounding."""
+    from oracle.phipm import IOM2Basis
+    rng = np.random.default_rng(7)
+    n, m = 60, 15
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    A = Q @ np.diag(np.linspace(-3.0, 2.0, n)) @ Q.T
+    v1 = rng.standard_normal(n)
+    v1 /= np.linalg.norm(v1)
+    H2 = IOM2Basis(lambda x: A @ x, v1, iom=2, m_max=m, bd=1e-13)
+    Hf = IOM2Basis(lambda x: A @ x, v1, iom=64, m_max=m, bd=1e-13)
+    H2.extend(m)
+    Hf.extend(m)
+    assert np.abs(Hf.H - H2.H).max() <= 1e-9
+    assert np.abs(np.triu(Hf.H[:m, :m], 2)).max() <= 1e-9
+
+
+@pytest.mark.parametrize("iom", [4, 64])
+def test_wide_window_phi_action_matches_dense_reference(iom):
+    s, u, A, Amul = _setup()
+    v = _vecs(s, (0, 1, 0, 1), seed=3)
+    W, st = phipm_simul_iom2(Amul, [0.5, 1.0], v, PhiOpts(tol=1e-12, iom=iom), s.nA)
+    for w, rho in zip(W, [0.5, 1.0]):
+        ref = phi_combination_dense(A, v, rho)
+        assert np.linalg.norm(w - ref) <= 1e-10 * np.linalg.norm(ref)
+    assert st.n_jv > 0
