@@ -346,6 +346,15 @@ int run_lincomb(const swe_grid* g, double* out, std::initializer_list<std::pair<
   return SWE_OK;
 }
 
+// -nu wl and -nu wld: the Laplacian weights of the dissipation -nu L (L x)
+// (Eq. eq:swdis), so that pass 2 adds it with one FMA per term.
+static void scaled_laplacian(const HostGrid& h, double nu, std::vector<double>& nwl, std::vector<double>& nwld) {
+  nwl.resize(h.wl.size());
+  nwld.resize(h.wld.size());
+  for (size_t k = 0; k < nwl.size(); ++k) nwl[k] = -nu * h.wl[k];
+  for (size_t k = 0; k < nwld.size(); ++k) nwld[k] = -nu * h.wld[k];
+}
+
 int upload_grid(swe_grid* g) {
   HostGrid& h = g->host;
   const size_t ng = h.ng;
@@ -357,11 +366,14 @@ int upload_grid(swe_grid* g) {
   const int32_t* d_nbr = nullptr;
   const double *d_nrm = nullptr, *d_wl = nullptr, *d_wld = nullptr, *d_nc = nullptr, *d_ndd = nullptr,
                *d_sdg = nullptr, *d_vc = nullptr, *d_vd = nullptr, *d_wlT = nullptr, *d_ncT = nullptr,
-               *d_vcT = nullptr, *d_area = nullptr;
+               *d_vcT = nullptr, *d_area = nullptr, *d_nwl = nullptr, *d_nwld = nullptr;
   // the kernels read the G diagonal ndd - sdg directly (table "sdg" of the
-  // device copy holds that difference)
+  // device copy holds that difference), and the dissipation's Laplacian
+  // weights with -nu folded in
   std::vector<double> gdg(h.sdg.size());
   for (size_t k = 0; k < gdg.size(); ++k) gdg[k] = h.ndd[k] - h.sdg[k];
+  std::vector<double> nwl, nwld;
+  scaled_laplacian(h, g->T.nu, nwl, nwld);
   Part parts[] = {
       {h.nbr.data(), h.nbr.size() * 4, (void**)&d_nbr},  {h.xyz.data(), h.xyz.size() * 8, (void**)&d_nrm},
       {h.wl.data(), h.wl.size() * 8, (void**)&d_wl},     {h.wld.data(), h.wld.size() * 8, (void**)&d_wld},
@@ -370,6 +382,7 @@ int upload_grid(swe_grid* g) {
       {h.vd.data(), h.vd.size() * 8, (void**)&d_vd},     {h.wlT.data(), h.wlT.size() * 8, (void**)&d_wlT},
       {h.ncT.data(), h.ncT.size() * 8, (void**)&d_ncT},  {h.vcT.data(), h.vcT.size() * 8, (void**)&d_vcT},
       {h.area.data(), h.area.size() * 8, (void**)&d_area},
+      {nwl.data(), nwl.size() * 8, (void**)&d_nwl},      {nwld.data(), nwld.size() * 8, (void**)&d_nwld},
   };
   size_t total = 0;
   for (auto& p : parts) total += (p.bytes + 255) & ~size_t(255);
@@ -397,6 +410,8 @@ int upload_grid(swe_grid* g) {
   T.ncT = d_ncT;
   T.vcT = d_vcT;
   T.area = d_area;
+  T.nwl = d_nwl;
+  T.nwld = d_nwld;
   return SWE_OK;
 }
 
@@ -457,9 +472,12 @@ int ensure_mixed(swe_grid* g) {
   };
   std::vector<double> gdg(h.sdg.size());
   for (size_t k = 0; k < gdg.size(); ++k) gdg[k] = h.ndd[k] - h.sdg[k];
+  std::vector<double> nwl, nwld;
+  scaled_laplacian(h, g->T.nu, nwl, nwld);
   TablesF& T = g->TF;
   Part parts[] = {{&h.xyz, &T.nrm}, {&h.wl, &T.wl},   {&h.wld, &T.wld}, {&h.nc, &T.nc},
-                  {&h.ndd, &T.ndd}, {&gdg, &T.gdg},   {&h.vc, &T.vc},   {&h.vd, &T.vd}};
+                  {&h.ndd, &T.ndd}, {&gdg, &T.gdg},   {&h.vc, &T.vc},   {&h.vd, &T.vd},
+                  {&nwl, &T.nwl},   {&nwld, &T.nwld}};
   size_t total = 0;
   for (auto& p : parts) total += (p.src->size() * 4 + 255) & ~size_t(255);
   CK(cudaMalloc(&g->dtabF, total));

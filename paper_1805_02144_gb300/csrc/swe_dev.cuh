@@ -21,6 +21,8 @@ struct TablesT {
   const R* __restrict__ nrm;   // [3][ng] unit normals
   const R* __restrict__ wl;    // [6][ng]
   const R* __restrict__ wld;   // [ng]
+  const R* __restrict__ nwl;   // [6][ng] -nu wl: the dissipation's Laplacian weights
+  const R* __restrict__ nwld;  // [ng]    -nu wld
   const R* __restrict__ nc;    // [3][6][ng]
   const R* __restrict__ ndd;   // [3][ng]
   const R* __restrict__ gdg;   // [3][ng] G diagonal (ndd - sdg of the host tables)
@@ -80,6 +82,17 @@ __device__ __forceinline__ R lap_cell(const TablesT<R>& T, int i, const int (&nb
   R acc = ldtab(T.wld + i) * ld(psi + i);
 #pragma unroll
   for (int k = 0; k < SLOTS; ++k) acc = fma(ldtab(T.wl + (size_t)k * T.ng + i), ld(psi + nb[k]), acc);
+  return acc;
+}
+
+// acc + sum_k w_k psi_{nbr_k} + wd_i psi_i for the weight tables (w, wd):
+// with (nwl, nwld) this adds the dissipation -nu L psi onto acc in seven FMAs.
+template <typename R>
+__device__ __forceinline__ R lap_acc(const TablesT<R>& T, const R* w, const R* wd, int i, const int (&nb)[SLOTS],
+                                     const R* psi, R acc) {
+  acc = fma(ldtab(wd + i), ld(psi + i), acc);
+#pragma unroll
+  for (int k = 0; k < SLOTS; ++k) acc = fma(ldtab(w + (size_t)k * T.ng + i), ld(psi + nb[k]), acc);
   return acc;
 }
 
@@ -248,7 +261,7 @@ __device__ __forceinline__ void pass2_cell(const TablesT<R>& T, int i, const R* 
   }
   if (MODE != MODE_Q) {  // dissipation -nu L (L x) on every variable
 #pragma unroll
-    for (int c = 0; c < 4; ++c) out[c] = fma(-T.nu, lap_cell(T, i, nb, Lp + (size_t)c * ng), out[c]);
+    for (int c = 0; c < 4; ++c) out[c] = lap_acc(T, T.nwl, T.nwld, i, nb, Lp + (size_t)c * ng, out[c]);
   }
 }
 
