@@ -426,35 +426,43 @@ __device__ __forceinline__ float shared_coef<float>(const Shared& sh, int r) { r
 // windows wider than two, iom > 2): z' = z - sum_r c_r raw_{lo+r} and, by
 // linearity, L z' = L z - sum_r c_r L raw_{lo+r} from the Laplacian planes
 // kept for every slot.  Returns |z'|^2 of the cell.
-template <typename R>
+template <typename R, bool IL>
 __device__ __forceinline__ R orth_window_pass1_cell(const TablesT<R>& T, int i, const R* z, const SubBufs<R>& B,
                                                     const R* Lbuf, int lo, int w, const Shared& sh, R* rnew,
                                                     R* Lnew, const R* u, R* sq, size_t n, int p) {
   const int ng = T.ng;
   int nb[SLOTS];
   load_nbr(T, i, nb);
-  R zp[4], nrm = R(0);
+  R zp[4], lz[4], nrm = R(0);
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
-    const size_t e = (size_t)c * ng + i;
-    R v = ld(z + e);
-    R lz = lap_cell(T, i, nb, z + (size_t)c * ng);
-    for (int r = 0; r < w; ++r) {
-      const R cr = shared_coef<R>(sh, r);
-      v = fma(-cr, ld(B.raw(lo + r, n, p) + e), v);
-      lz = fma(-cr, ld(Lbuf + (size_t)(lo + r) * n + e), lz);
-    }
-    zp[c] = v;
-    rnew[e] = v;
-    Lnew[e] = lz;
-    nrm = fma(v, v, nrm);
+    zp[c] = ld(z + (size_t)c * ng + i);
+    lz[c] = lap_cell(T, i, nb, z + (size_t)c * ng);
   }
-  R uv[4];
+  for (int r = 0; r < w; ++r) {
+    const R cr = shared_coef<R>(sh, r);
+    const R* rr = B.raw(lo + r, n, p);
+    R Lr[4];
+    ld_planes<IL>(Lbuf + (size_t)(lo + r) * n, ng, i, Lr);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      zp[c] = fma(-cr, ld(rr + (size_t)c * ng + i), zp[c]);
+      lz[c] = fma(-cr, Lr[c], lz[c]);
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    rnew[(size_t)c * ng + i] = zp[c];
+    nrm = fma(zp[c], zp[c], nrm);
+  }
+  st_planes<IL>(Lnew, ng, i, lz);
+  R uv[4], sv[4];
 #pragma unroll
   for (int c = 0; c < 4; ++c) uv[c] = ld(u + (size_t)c * ng + i);
-  sq[i] = fma(uv[0], zp[0], fma(uv[1], zp[1], fma(uv[2], zp[2], T.g * zp[3])));
+  sv[0] = fma(uv[0], zp[0], fma(uv[1], zp[1], fma(uv[2], zp[2], T.g * zp[3])));
 #pragma unroll
-  for (int c = 0; c < 3; ++c) sq[(size_t)(1 + c) * ng + i] = fma(zp[c], uv[3], uv[c] * zp[3]);
+  for (int c = 0; c < 3; ++c) sv[1 + c] = fma(zp[c], uv[3], uv[c] * zp[3]);
+  st_planes<IL>(sq, ng, i, sv);
   return nrm;
 }
 
@@ -475,6 +483,8 @@ __device__ bool phi_run(const PhiArgsT<R>& a, Shared& sh) {
   // happy-breakdown threshold relative to the window coefficients: near the
   // rounding floor of the basis precision
   const double bd = sizeof(R) == 8 ? 1e-13 : 1e-6;
+  // FP32: pass-1 planes interleaved, one 16-byte vector per cell
+  constexpr bool IL = sizeof(R) == 4;
   const int ng = T.ng;
   const size_t n = (size_t)4 * ng;
   const int p = a.p;
@@ -579,7 +589,7 @@ __device__ bool phi_run(const PhiArgsT<R>& a, Shared& sh) {
         R* wj = B.Wk + (size_t)j * n;
         if (nz_prev) {
           FOR_CELLS(i)
-            pass1_cell<MODE_J>(T, i, wprev, R(1), a.u_lin, a.tmp, a.tmp + (size_t)4 * ng);
+            pass1_cell<MODE_J, R, IL>(T, i, wprev, R(1), a.u_lin, a.tmp, a.tmp + (size_t)4 * ng);
           if (!grid_barrier(a, sh, PH_W_PASS1)) return false;
         }
         R clr[PMAX + 1];
@@ -589,7 +599,7 @@ __device__ bool phi_run(const PhiArgsT<R>& a, Shared& sh) {
         R sqs = R(0);
         FOR_CELLS(i) {
           R o[4] = {R(0), R(0), R(0), R(0)};
-          if (nz_prev) pass2_cell<MODE_J>(T, i, wprev, R(1), a.tmp, a.tmp + (size_t)4 * ng, a.aux, o);
+          if (nz_prev) pass2_cell<MODE_J, R, IL>(T, i, wprev, R(1), a.tmp, a.tmp + (size_t)4 * ng, a.aux, o);
 #pragma unroll
           for (int c = 0; c < 4; ++c) {
             const size_t e = (size_t)c * ng + i;
@@ -654,13 +664,13 @@ __device__ bool phi_run(const PhiArgsT<R>& a, Shared& sh) {
             const double sj = vld(&C->sig[j]);
             if (j == 0) {
               FOR_CELLS(i)
-                pass1_cell<MODE_J>(T, i, rj, R(1), a.u_lin, Lj, SQ);
+                pass1_cell<MODE_J, R, IL>(T, i, rj, R(1), a.u_lin, Lj, SQ);
               if (!grid_barrier(a, sh, PH_K_PASS1)) return false;
             }
             const R zs = (R)(a.dt * sj);
             FOR_CELLS(i) {
               R o[4];
-              pass2_cell<MODE_J>(T, i, rj, R(1), Lj, SQ, a.aux, o);
+              pass2_cell<MODE_J, R, IL>(T, i, rj, R(1), Lj, SQ, a.aux, o);
 #pragma unroll
               for (int c = 0; c < 4; ++c) a.Zbuf[(size_t)c * ng + i] = zs * o[c];
             }
@@ -698,7 +708,7 @@ __device__ bool phi_run(const PhiArgsT<R>& a, Shared& sh) {
             __syncthreads();
             R nrm = R(0);
             FOR_CELLS(i)
-              nrm += orth_window_pass1_cell(T, i, a.Zbuf, B, a.Lbuf, lo, w, sh, rj1, Lj1, a.u_lin, SQ, n, p);
+              nrm += orth_window_pass1_cell<R, IL>(T, i, a.Zbuf, B, a.Lbuf, lo, w, sh, rj1, Lj1, a.u_lin, SQ, n, p);
             double wn[1] = {(double)nrm};
             GridSync* gs = a.sync;
             auto post_wnorm = [gs, j, lo, w, bd](volatile PhiCtrl* c, bool leader, const auto& r) {
@@ -738,14 +748,14 @@ __device__ bool phi_run(const PhiArgsT<R>& a, Shared& sh) {
             const double sjm = j > 0 ? vld(&C->sig[j - 1]) : 0.0;
             if (j == 0) {
               FOR_CELLS(i)
-                pass1_cell<MODE_J>(T, i, rj, R(1), a.u_lin, Lj, SQ);
+                pass1_cell<MODE_J, R, IL>(T, i, rj, R(1), a.u_lin, Lj, SQ);
               if (!grid_barrier(a, sh, PH_K_PASS1)) return false;
             }
             const R zs = (R)(a.dt * sj);
             R d0 = R(0), d1 = R(0);
             FOR_CELLS(i) {
               R o[4];
-              pass2_cell<MODE_J>(T, i, rj, R(1), Lj, SQ, a.aux, o);
+              pass2_cell<MODE_J, R, IL>(T, i, rj, R(1), Lj, SQ, a.aux, o);
 #pragma unroll
               for (int c = 0; c < 4; ++c) {
                 const size_t e = (size_t)c * ng + i;
@@ -768,7 +778,7 @@ __device__ bool phi_run(const PhiArgsT<R>& a, Shared& sh) {
             const R aj = (R)(hdj * sj);
             R nrm = R(0);
             FOR_CELLS(i)
-              nrm += orth_pass1_cell(T, i, a.Zbuf, rj, rjm, aj, am, Lj, Ljm, rj1, Lj1, a.u_lin, SQ);
+              nrm += orth_pass1_cell<R, IL>(T, i, a.Zbuf, rj, rjm, aj, am, Lj, Ljm, rj1, Lj1, a.u_lin, SQ);
             double w[1] = {(double)nrm};
             GridSync* gs = a.sync;
             auto post_norm = [gs, j, bd, hdj, huj](volatile PhiCtrl* c, bool leader, const auto& r) {

@@ -85,21 +85,39 @@ __device__ __forceinline__ R lap_cell(const TablesT<R>& T, int i, const int (&nb
   return acc;
 }
 
-// acc + sum_k w_k psi_{nbr_k} + wd_i psi_i for the weight tables (w, wd):
-// with (nwl, nwld) this adds the dissipation -nu L psi onto acc in seven FMAs.
-template <typename R>
-__device__ __forceinline__ R lap_acc(const TablesT<R>& T, const R* w, const R* wd, int i, const int (&nb)[SLOTS],
-                                     const R* psi, R acc) {
-  acc = fma(ldtab(wd + i), ld(psi + i), acc);
-#pragma unroll
-  for (int k = 0; k < SLOTS; ++k) acc = fma(ldtab(w + (size_t)k * T.ng + i), ld(psi + nb[k]), acc);
-  return acc;
-}
-
 template <typename R>
 __device__ __forceinline__ void load_nbr(const TablesT<R>& T, int i, int (&nb)[SLOTS]) {
 #pragma unroll
   for (int k = 0; k < SLOTS; ++k) nb[k] = ldtabi(T.nbr + (size_t)k * T.ng + i);
+}
+
+// The pass-1 planes (4 Laplacian, 4 scalar/vector) are planar, [4][ng], or
+// with IL interleaved, [ng][4]: one 16-byte vector per cell, so that a
+// neighbour's four values come in one gather.  IL is used by the FP32
+// instantiations only; the arithmetic is the same in both layouts.
+template <bool IL, typename R>
+__device__ __forceinline__ void st_planes(R* base, int ng, int i, const R (&v)[4]) {
+  if constexpr (IL) {
+    static_assert(sizeof(R) == 4, "interleaved planes are FP32");
+    *reinterpret_cast<float4*>(base + 4 * (size_t)i) = make_float4(v[0], v[1], v[2], v[3]);
+  } else {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) base[(size_t)c * ng + i] = v[c];
+  }
+}
+template <bool IL, typename R>
+__device__ __forceinline__ void ld_planes(const R* base, int ng, int i, R (&v)[4]) {
+  if constexpr (IL) {
+    static_assert(sizeof(R) == 4, "interleaved planes are FP32");
+    const float4 q = *reinterpret_cast<const float4*>(base + 4 * (size_t)i);
+    v[0] = q.x;
+    v[1] = q.y;
+    v[2] = q.z;
+    v[3] = q.w;
+  } else {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) v[c] = ld(base + (size_t)c * ng + i);
+  }
 }
 
 // Pass 1 of a stencil at cell i.  Writes four Laplacian planes to Lout and
@@ -107,7 +125,7 @@ __device__ __forceinline__ void load_nbr(const TablesT<R>& T, int i, int (&nb)[S
 //   MODE_F: x = u.          L u (4), E = |u|^2/2 + g (h + h_s), q = u h
 //   MODE_J: x = sx * xraw.  L x (4), s = u.x_u + g x_h,  q = x_u h + u x_h
 //   MODE_Q: x = d.          -,       E = |d_u|^2/2,      q = d_u d_h
-template <int MODE, typename R>
+template <int MODE, typename R, bool IL = false>
 __device__ __forceinline__ void pass1_cell(const TablesT<R>& T, int i, const R* x, R sx, const R* u,
                                            R* Lout, R* sq) {
   const int ng = T.ng;
@@ -117,31 +135,35 @@ __device__ __forceinline__ void pass1_cell(const TablesT<R>& T, int i, const R* 
 #pragma unroll
   for (int c = 0; c < 4; ++c) xv[c] = ld(x + (size_t)c * ng + i);
   if (MODE != MODE_Q) {
+    R lv[4];
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       R lx = lap_cell(T, i, nb, x + (size_t)c * ng);
-      Lout[(size_t)c * ng + i] = (MODE == MODE_J) ? sx * lx : lx;
+      lv[c] = (MODE == MODE_J) ? sx * lx : lx;
     }
+    st_planes<IL>(Lout, ng, i, lv);
   }
+  R sv[4];
   if (MODE == MODE_J) {
 #pragma unroll
     for (int c = 0; c < 4; ++c) xv[c] *= sx;
     R uv[4];
 #pragma unroll
     for (int c = 0; c < 4; ++c) uv[c] = ld(u + (size_t)c * ng + i);
-    sq[i] = fma(uv[0], xv[0], fma(uv[1], xv[1], fma(uv[2], xv[2], T.g * xv[3])));
+    sv[0] = fma(uv[0], xv[0], fma(uv[1], xv[1], fma(uv[2], xv[2], T.g * xv[3])));
 #pragma unroll
-    for (int c = 0; c < 3; ++c) sq[(size_t)(1 + c) * ng + i] = fma(xv[c], uv[3], uv[c] * xv[3]);
+    for (int c = 0; c < 3; ++c) sv[1 + c] = fma(xv[c], uv[3], uv[c] * xv[3]);
   } else if (MODE == MODE_F) {
     const R hsurf = T.hs ? ld(T.hs + i) : R(0);  // E = |u|^2/2 + g (h + h_s)
-    sq[i] = fma(R(0.5), fma(xv[0], xv[0], fma(xv[1], xv[1], xv[2] * xv[2])), T.g * (xv[3] + hsurf));
+    sv[0] = fma(R(0.5), fma(xv[0], xv[0], fma(xv[1], xv[1], xv[2] * xv[2])), T.g * (xv[3] + hsurf));
 #pragma unroll
-    for (int c = 0; c < 3; ++c) sq[(size_t)(1 + c) * ng + i] = xv[c] * xv[3];
+    for (int c = 0; c < 3; ++c) sv[1 + c] = xv[c] * xv[3];
   } else {
-    sq[i] = R(0.5) * fma(xv[0], xv[0], fma(xv[1], xv[1], xv[2] * xv[2]));
+    sv[0] = R(0.5) * fma(xv[0], xv[0], fma(xv[1], xv[1], xv[2] * xv[2]));
 #pragma unroll
-    for (int c = 0; c < 3; ++c) sq[(size_t)(1 + c) * ng + i] = xv[c] * xv[3];
+    for (int c = 0; c < 3; ++c) sv[1 + c] = xv[c] * xv[3];
   }
+  st_planes<IL>(sq, ng, i, sv);
 }
 
 // Fused IOM2 orthogonalisation and pass 1 (MODE_J) at cell i.  z is A v_j
@@ -153,34 +175,39 @@ __device__ __forceinline__ void pass1_cell(const TablesT<R>& T, int i, const R* 
 //   s', q' of z'                                      -> sq
 // and returns |z'|^2 of the cell.  No value of z' is gathered, so rnew may be
 // written while neighbours still read z.
-template <typename R>
+template <typename R, bool IL = false>
 __device__ __forceinline__ R orth_pass1_cell(const TablesT<R>& T, int i, const R* z, const R* rj,
                                              const R* rm, R aj, R am, const R* Lj, const R* Lm,
                                              R* rnew, R* Lnew, const R* u, R* sq) {
   const int ng = T.ng;
   int nb[SLOTS];
   load_nbr(T, i, nb);
+  R Ljv[4], Lmv[4] = {R(0), R(0), R(0), R(0)}, lzv[4];
+  ld_planes<IL>(Lj, ng, i, Ljv);
+  if (rm) ld_planes<IL>(Lm, ng, i, Lmv);
   R zp[4], nrm = R(0);
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
     const size_t e = (size_t)c * ng + i;
     R v = fma(-aj, ld(rj + e), ld(z + e));
-    R lz = fma(-aj, ld(Lj + e), lap_cell(T, i, nb, z + (size_t)c * ng));
+    R lz = fma(-aj, Ljv[c], lap_cell(T, i, nb, z + (size_t)c * ng));
     if (rm) {
       v = fma(-am, ld(rm + e), v);
-      lz = fma(-am, ld(Lm + e), lz);
+      lz = fma(-am, Lmv[c], lz);
     }
     zp[c] = v;
     rnew[e] = v;
-    Lnew[e] = lz;
+    lzv[c] = lz;
     nrm = fma(v, v, nrm);
   }
-  R uv[4];
+  st_planes<IL>(Lnew, ng, i, lzv);
+  R uv[4], sv[4];
 #pragma unroll
   for (int c = 0; c < 4; ++c) uv[c] = ld(u + (size_t)c * ng + i);
-  sq[i] = fma(uv[0], zp[0], fma(uv[1], zp[1], fma(uv[2], zp[2], T.g * zp[3])));
+  sv[0] = fma(uv[0], zp[0], fma(uv[1], zp[1], fma(uv[2], zp[2], T.g * zp[3])));
 #pragma unroll
-  for (int c = 0; c < 3; ++c) sq[(size_t)(1 + c) * ng + i] = fma(zp[c], uv[3], uv[c] * zp[3]);
+  for (int c = 0; c < 3; ++c) sv[1 + c] = fma(zp[c], uv[3], uv[c] * zp[3]);
+  st_planes<IL>(sq, ng, i, sv);
   return nrm;
 }
 
@@ -189,7 +216,7 @@ __device__ __forceinline__ R orth_pass1_cell(const TablesT<R>& T, int i, const R
 //   Lp, sq: the planes pass 1 wrote (Laplacian, scalar + vector)
 //   aux (MODE_J only): [eta, P_x, P_y, P_z] of the linearisation state,
 //   eta = V u + f, P = n x u.
-template <int MODE, typename R>
+template <int MODE, typename R, bool IL = false>
 __device__ __forceinline__ void pass2_cell(const TablesT<R>& T, int i, const R* x, R sx, const R* Lp,
                                            const R* sq, const R* aux, R out[4]) {
   const int ng = T.ng;
@@ -207,22 +234,23 @@ __device__ __forceinline__ void pass2_cell(const TablesT<R>& T, int i, const R* 
       vor = fma(ldtab(T.vc + ((size_t)c * SLOTS + k) * ng + i), ld(x + (size_t)c * ng + j), vor);
   }
   // gradient of the scalar plane (before projection) and divergence of the vector planes
-  const R sci = ld(sq + i);
+  R sqi[4];
+  ld_planes<IL>(sq, ng, i, sqi);
   R gr[3], dv = R(0);
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    gr[c] = ldtab(T.gdg + (size_t)c * ng + i) * sci;
-    dv = fma(ldtab(T.ndd + (size_t)c * ng + i), ld(sq + (size_t)(1 + c) * ng + i), dv);
+    gr[c] = ldtab(T.gdg + (size_t)c * ng + i) * sqi[0];
+    dv = fma(ldtab(T.ndd + (size_t)c * ng + i), sqi[1 + c], dv);
   }
 #pragma unroll
   for (int k = 0; k < SLOTS; ++k) {
-    const int j = nb[k];
-    const R scj = ld(sq + j);
+    R sqj[4];
+    ld_planes<IL>(sq, ng, nb[k], sqj);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       R w = ldtab(T.nc + ((size_t)c * SLOTS + k) * ng + i);
-      gr[c] = fma(w, scj, gr[c]);
-      dv = fma(w, ld(sq + (size_t)(1 + c) * ng + j), dv);
+      gr[c] = fma(w, sqj[0], gr[c]);
+      dv = fma(w, sqj[1 + c], dv);
     }
   }
   R n0 = ldtab(T.nrm + i), n1 = ldtab(T.nrm + ng + i), n2 = ldtab(T.nrm + 2 * (size_t)ng + i);
@@ -259,9 +287,19 @@ __device__ __forceinline__ void pass2_cell(const TablesT<R>& T, int i, const R* 
     out[2] = -fma(vor, nx2, gr[2]);
     out[3] = -dv;
   }
-  if (MODE != MODE_Q) {  // dissipation -nu L (L x) on every variable
+  if (MODE != MODE_Q) {  // dissipation -nu L (L x) on every variable: (nwl, nwld) hold -nu L
+    R Lv[4];
+    ld_planes<IL>(Lp, ng, i, Lv);
+    const R wd = ldtab(T.nwld + i);
 #pragma unroll
-    for (int c = 0; c < 4; ++c) out[c] = lap_acc(T, T.nwl, T.nwld, i, nb, Lp + (size_t)c * ng, out[c]);
+    for (int c = 0; c < 4; ++c) out[c] = fma(wd, Lv[c], out[c]);
+#pragma unroll
+    for (int k = 0; k < SLOTS; ++k) {
+      ld_planes<IL>(Lp, ng, nb[k], Lv);
+      const R w = ldtab(T.nwl + (size_t)k * ng + i);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) out[c] = fma(w, Lv[c], out[c]);
+    }
   }
 }
 
