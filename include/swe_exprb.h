@@ -329,6 +329,17 @@ int swe_ensemble_tune(swe_ensemble* ens, int rounds, void* stream);
 int swe_ensemble_stats(swe_ensemble* ens, phi_stats* stats, double* member_ms, int* member_blocks,
                        void* stream);
 
+/* Self-test of the failure path of every device-side wait: one block whose
+ * thread 0 polls, exactly as the grid barriers do, a flag that nothing sets.
+ * The wait gives up after limit_ns of device time (1e3 <= limit_ns <= 1e9)
+ * and the kernel returns normally; with preset_abort (a SWE_ERR_* code, or
+ * 0) stored in the abort word first, it ends at the first check instead.
+ * *status_out (host) receives the abort word: SWE_ERR_TIMEOUT when the wait
+ * ran out, preset_abort when that was set.  The context stays usable.
+ * Returns SWE_ERR_INVALID_ARG for a limit out of range, SWE_ERR_CUDA if the
+ * launch or copies fail.  Synchronises `stream`. */
+int swe_selftest_wait(int64_t limit_ns, int preset_abort, int* status_out, void* stream);
+
 /* Waits for `stream` and returns the first device-side error of the grid's
  * last phi_action / exprb_step (SWE_OK if none), clearing it. */
 int swe_device_status(swe_grid* grid, void* stream);

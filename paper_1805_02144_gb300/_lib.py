@@ -16,6 +16,7 @@ import numpy as np
 from . import build as _build
 
 SWE_OK = 0
+SWE_ERR_INVALID_ARG, SWE_ERR_NOMEM, SWE_ERR_NOCONV, SWE_ERR_NONFINITE, SWE_ERR_TIMEOUT, SWE_ERR_CUDA = -1, -2, -3, -4, -5, -6
 ERRORS = {-1: "INVALID_ARG", -2: "NOMEM", -3: "NOCONV", -4: "NONFINITE", -5: "TIMEOUT", -6: "CUDA"}
 SCHEMES = {"epi2": 0, "exprb42": 1, "pexprb43": 2, "exprb53": 3, "epi3": 4}
 
@@ -27,7 +28,7 @@ EXPORTS = ["swe_phi_opts_default", "swe_create_grid", "swe_create_grid_host", "s
            "exprb_step", "exprb_step_adjoint", "swe_profile_enable", "swe_profile_read", "swe_device_status",
            "swe_last_error", "swe_ensemble_create", "swe_ensemble_destroy", "swe_ensemble_set_state",
            "swe_ensemble_get_state", "swe_ensemble_run", "swe_ensemble_reset", "swe_ensemble_tune",
-           "swe_ensemble_stats"]
+           "swe_ensemble_stats", "swe_selftest_wait"]
 
 
 class PhiOptsC(C.Structure):
@@ -110,6 +111,7 @@ def load(path: Optional[str] = None) -> C.CDLL:
     L.swe_profile_enable.argtypes = [vp, C.c_int]
     L.swe_profile_read.argtypes = [vp, C.POINTER(ProfileC), vp]
     L.swe_device_status.argtypes = [vp, vp]
+    L.swe_selftest_wait.argtypes = [C.c_int64, C.c_int, C.POINTER(C.c_int), vp]
     L.swe_ensemble_create.argtypes = [C.POINTER(vp), C.c_int, dp, C.POINTER(C.c_int),
                                       C.POINTER(PhiOptsC), C.POINTER(vp)]
     L.swe_ensemble_destroy.argtypes = [vp]
@@ -128,7 +130,7 @@ def load(path: Optional[str] = None) -> C.CDLL:
                  "swe_scheme_state_reset", "exprb_step", "exprb_step_adjoint", "swe_device_status", "swe_profile_enable",
                  "swe_profile_read", "swe_ensemble_create", "swe_ensemble_set_state",
                  "swe_ensemble_get_state", "swe_ensemble_run", "swe_ensemble_reset", "swe_ensemble_tune",
-                 "swe_ensemble_stats"):
+                 "swe_ensemble_stats", "swe_selftest_wait"):
         getattr(L, name).restype = C.c_int
     _LIB = L
     return L

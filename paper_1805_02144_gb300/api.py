@@ -302,6 +302,14 @@ def exprb_step_differentiable(grid: Grid, scheme: str, dt: float, u_n: torch.Ten
     return ExprbStepFunction.apply(u_n, grid, scheme, dt, state, opts, trace_cap)
 
 
+def swe_selftest_wait(limit_s: float = 0.02, preset_abort: int = 0, stream=None) -> int:
+    """Run the bounded device-side wait on a flag that nothing sets; returns the
+    abort word it left (SWE_ERR_TIMEOUT, or preset_abort if one was given)."""
+    st = C.c_int(0)
+    check(load().swe_selftest_wait(int(limit_s * 1e9), int(preset_abort), C.byref(st), _stream(stream)))
+    return st.value
+
+
 def swe_device_status(grid: Grid, stream=None) -> None:
     check(load().swe_device_status(grid.handle, _stream(stream)))
 

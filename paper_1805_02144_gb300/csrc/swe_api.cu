@@ -346,6 +346,15 @@ int run_lincomb(const swe_grid* g, double* out, std::initializer_list<std::pair<
   return SWE_OK;
 }
 
+// Thread 0 waits, with the poll of every grid barrier, for a flag that nothing
+// sets; the wait ends at the time limit (or at once on a set abort word) and
+// the kernel returns normally with the reason in s->abort.
+__global__ void k_selftest_wait(GridSync* s, const int* flag, unsigned long long limit_ns) {
+  if (threadIdx.x != 0) return;
+  const volatile int* f = flag;
+  bounded_spin(s, SWE_ERR_TIMEOUT, [&] { return *f == 0; }, limit_ns);
+}
+
 // -nu wl and -nu wld: the Laplacian weights of the dissipation -nu L (L x)
 // (Eq. eq:swdis), so that pass 2 adds it with one FMA per term.
 static void scaled_laplacian(const HostGrid& h, double nu, std::vector<double>& nwl, std::vector<double>& nwld) {
@@ -1988,6 +1997,33 @@ int swe_profile_read(swe_grid* g, swe_profile* out, void* stream) {
   out->phi_table_bytes = dp.table_bytes;
   for (int k = 0; k < 10; ++k) out->phase_ms[k] = 1e-6 * (double)dp.phase_ns[k];
   return SWE_OK;
+}
+
+int swe_selftest_wait(int64_t limit_ns, int preset_abort, int* status_out, void* stream) {
+  if (!status_out || limit_ns < 1000 || limit_ns > 1000000000) return fail(SWE_ERR_INVALID_ARG, "swe_selftest_wait: 1 us <= limit_ns <= 1 s");
+  if (preset_abort > 0) return fail(SWE_ERR_INVALID_ARG, "swe_selftest_wait: preset_abort is 0 or a SWE_ERR_* code");
+  struct Block {
+    GridSync sync;
+    int flag;
+  };
+  Block* d = nullptr;
+  CK(cudaMalloc(&d, sizeof(Block)));
+  int rc = SWE_OK;
+  int abort_word = 0;
+  cudaError_t e = cudaMemsetAsync(d, 0, sizeof(Block), S(stream));
+  if (e == cudaSuccess && preset_abort != 0)
+    e = cudaMemcpyAsync(&d->sync.abort, &preset_abort, sizeof(int), cudaMemcpyHostToDevice, S(stream));
+  if (e == cudaSuccess) {
+    k_selftest_wait<<<1, 32, 0, S(stream)>>>(&d->sync, &d->flag, (unsigned long long)limit_ns);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&abort_word, &d->sync.abort, sizeof(int), cudaMemcpyDeviceToHost, S(stream));
+  if (e == cudaSuccess) e = cudaStreamSynchronize(S(stream));
+  cudaFree(d);
+  if (e != cudaSuccess) rc = fail(SWE_ERR_CUDA, cudaGetErrorString(e));
+  *status_out = abort_word;
+  return rc;
 }
 
 int swe_device_status(swe_grid* g, void* stream) {

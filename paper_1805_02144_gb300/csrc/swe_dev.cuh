@@ -464,9 +464,11 @@ __device__ __forceinline__ unsigned int flip_arrive(GridSync* s, int gb, int gn,
 }
 
 // Bounded spin until cond() is false; checks the abort word and the time
-// limit every 64 polls.  Returns false on abort or timeout.
+// limit (kWaitNs unless given) every 64 polls.  Returns false on abort or
+// timeout.
 template <class Cond>
-__device__ __forceinline__ bool bounded_spin(GridSync* s, int timeout_code, Cond cond) {
+__device__ __forceinline__ bool bounded_spin(GridSync* s, int timeout_code, Cond cond,
+                                             unsigned long long limit_ns = kWaitNs) {
   unsigned long long t0 = 0;
   for (unsigned int it = 0; cond(); ++it) {
     if ((it & 63u) == 63u) {
@@ -474,7 +476,7 @@ __device__ __forceinline__ bool bounded_spin(GridSync* s, int timeout_code, Cond
       const unsigned long long now = globaltimer();
       if (t0 == 0) {
         t0 = now;
-      } else if (now - t0 > kWaitNs) {
+      } else if (now - t0 > limit_ns) {
         atomicCAS(&s->abort, 0, timeout_code);
         return false;
       }
