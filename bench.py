@@ -205,20 +205,43 @@ def timed_steps(G, u0, scheme, dt, nsteps, opts, flush, state=None, profile=Fals
 
 
 def precision_block(flush) -> dict:
-    """Mixed precision vs FP64 on the level-8 exprb53 12 h run (same state)."""
+    """Mixed precision vs FP64 on the level-8 exprb53 12 h run (same state),
+    and the same comparison on the level-9 grid."""
+    out = precision_run(flush, 8)
+    try:
+        lv9 = precision_run(flush, 9)
+        out["level9"] = {k: lv9[k] for k in ("workload", "mixed", "fp64", "speedup_mixed_over_fp64",
+                                             "rel_l2_mixed_vs_fp64")}
+    except Exception as e:  # recorded, never fatal to the bench line
+        out["level9"] = {"error": f"{e!s:.300}"}
+    return out
+
+
+def precision_run(flush, level: int) -> dict:
     import torch
     from paper_1805_02144_gb300.api import Grid
     from paper_1805_02144_gb300.inputs import balanced_state
-    G = Grid(8)
+    G = Grid(level)
     ng = G.ncells
     u0 = torch.from_numpy(balanced_state(G.cell_centres(), 3, 400.0)).cuda()
     res = {}
+    from paper_1805_02144_gb300.api import SchemeState, exprb_step
+
+    def replay_status(opts) -> dict:
+        """The same 24 steps, untimed, with every step's device status and Krylov size."""
+        st, u, codes, mmax = SchemeState(G), u0.clone(), [], 0
+        for _ in range(24):
+            u, info = exprb_step(G, "exprb53", 1800.0, u, state=st, opts=opts, stats=True)
+            codes.append(info["status"])
+            mmax = max(mmax, info["m_max_used"])
+        bad = [k for k, c in enumerate(codes) if c != 0]
+        return {"status": codes[bad[0]] if bad else 0, "steps_with_status": bad, "m_max_used": mmax}
     for name, opts in (("mixed", {"precision": 1, "tol": 1e-6}), ("fp64", {"tol": 1e-8})):
         timed_steps(G, u0, "exprb53", 1800.0, 2, opts, flush)          # warm-up
         ms, u, prof = timed_steps(G, u0, "exprb53", 1800.0, 24, opts, flush, profile=True)
         tot = sum(ms)
         res[name] = {"steps_per_s": 24 / (tot / 1e3), "ms_per_step": tot / 24, "tol": opts["tol"],
-                     "phi_share": prof["phi_ms"] / tot, "state": u}
+                     "phi_share": prof["phi_ms"] / tot, "state": u, **replay_status(opts)}
         if name == "mixed":
             gbs = prof["phi_bytes"] / (prof["phi_ms"] / 1e3) / 1e9
             hbm = _peaks().get("hbm_gbs", 6779.0)
@@ -232,7 +255,7 @@ def precision_block(flush) -> dict:
     a, b = res["mixed"].pop("state").cpu().numpy(), res["fp64"].pop("state").cpu().numpy()
     eh = float(np.linalg.norm(a[3 * ng:] - b[3 * ng:]) / np.linalg.norm(b[3 * ng:]))
     ev = float(np.linalg.norm(a[:3 * ng] - b[:3 * ng]) / np.linalg.norm(b[:3 * ng]))
-    return {"workload": "exprb53, level-8 grid (655362 cells, n=2621448), dt=1800 s, 12 h "
+    return {"workload": f"exprb53, level-{level} grid ({ng} cells, n={4 * ng}), dt=1800 s, 12 h "
                         "(24 steps from the same seeded state, seed 3, 400 m)",
             "mixed": res["mixed"], "fp64": res["fp64"],
             "speedup_mixed_over_fp64": res["mixed"]["steps_per_s"] / res["fp64"]["steps_per_s"],
