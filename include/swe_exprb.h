@@ -246,8 +246,8 @@ int exprb_step(swe_grid* grid, int scheme, double dt, const double* u_n, double*
  *     wrote them into phi_stats.trace (call indices 0..ncalls-1 in order).
  *   lam_np1: device, n doubles, adjoint of u_{n+1}; lam_n: device output,
  *     must not alias lam_np1 or u_n.
- *   opts: NULL or FP64 options (precision must be 0); the replay fields are
- *     ignored (the trace is the replay).
+ *   opts: NULL or FP64 options (precision must be 0, iom must be 2); the
+ *     replay fields are ignored (the trace is the replay).
  * The step is recomputed from u_n in replay mode with every accepted
  * substep's w_j, Krylov basis and small matrices kept on a device tape
  * (grown as needed and owned by the grid), then one persistent launch per
@@ -309,11 +309,13 @@ int swe_profile_read(swe_grid* grid, swe_profile* out, void* stream);
  * restores the states and the carried Krylov sizes), fits each member's group
  * time as serial + parallel / blocks from its last two runs, re-splits to
  * minimise the predicted longest group, and finally keeps the split whose
- * measured longest group was shortest (3 or more rounds use the fit).  Each member carries its last accepted Krylov size
- * per call from step to step and from run to run (m carry);
+ * measured longest group was shortest (3 or more rounds use the fit).
+ * Each member carries its last accepted Krylov size per call from step to
+ * step and from run to run (m carry);
  * swe_ensemble_reset clears it, as for a new trajectory.
- * opts: FP64 only (precision 0), no replay.  All grids must be device grids
- * on the current device. */
+ * opts: FP64 only (precision 0), iom = 2, no replay (else
+ * SWE_ERR_INVALID_ARG).  All grids must be device grids on the current
+ * device. */
 typedef struct swe_ensemble swe_ensemble;
 int swe_ensemble_create(swe_grid* const* grids, int nmem, const double* dt, const int* nsteps,
                         const phi_opts* opts, swe_ensemble** out);
