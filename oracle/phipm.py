@@ -55,10 +55,14 @@ R9  Substeps land exactly on each rho_i: tau_k = rho_i - t_k whenever
     does not shrink later substeps.  tau and m carry over to the next output.
 R10 Zero skip (step 1): A w_{j-1} is skipped when w_{j-1} is exactly zero.
 R11 Bounds (not in the paper): a call fails with NoConvergence after
-    max_substeps accepted substeps, when an accepted substep would not move
-    t, or when ||tau Hhat_m||_1 exceeds HNORM_MAX = 4096 (the GPU's scaled
-    Taylor exponential would need more than 1024 scaling steps), so a run
-    whose state or step size has gone wrong ends instead of running on.
+    max_substeps accepted substeps (an option), after max_reject rejections,
+    when an accepted substep would not move t, or when the error estimate is
+    not finite, so a run whose state or step size has gone wrong ends instead
+    of running on.  The exponential itself has no size limit here.
+
+The controller of steps 4-6 is split into three functions, each pinned on its
+own: ``cost`` (Eq. (eq:cost)), ``proposals`` (step 4, R8) and
+``prefer_step_size`` (step 5, R8); ``accepts`` is the test of step 6.
 """
 from __future__ import annotations
 
@@ -73,9 +77,6 @@ from .phi import augmented_norm1, phi_krylov
 
 class NoConvergence(RuntimeError):
     pass
-
-
-HNORM_MAX = 4096.0   # R11
 
 
 @dataclasses.dataclass
@@ -118,11 +119,48 @@ def nint(x: float) -> int:
 
 
 def cost(tau: float, m: int, p: int, remaining: float, N: int, nA: int, hnorm: float) -> float:
-    """C(tau, m) of Eq. (eq:cost); hnorm = ||tau Hhat_m||_1."""
+    """C(tau, m) of Eq. (eq:cost); hnorm = ||tau Hhat_m||_1, remaining = t_out - t_k.
+
+    Readings (R8): the substep count nint(remaining / tau) is at least 1, and
+    the nint of M's logarithm is at least 0 (so M >= 44/3 for small norms).
+    """
     nsub = max(1, nint(remaining / tau))
     M = 44.0 / 3.0 + 2.0 * max(0, nint(math.log2(hnorm / 5.37)))
     return (nsub * m * (N + nA) + 2 * (p - 1) * (nA + N)
             + M * (m + p + 1) ** 3 + (2 * p + 1) * N)
+
+
+def accepts(omega: float, delta: float) -> bool:
+    """Algorithm 1 step 6: accept the substep when t_out eps / (tau Tol s) <= delta."""
+    return omega <= delta
+
+
+def proposals(omega: float, tau: float, m: int, cap: int, opts: "PhiOpts") -> tuple[float, int]:
+    """Algorithm 1 step 4 (reading R8): (tau_new, m_new) from omega of the attempt (tau, m).
+
+    cap: the largest usable Krylov size (m_max, or the breakdown size).
+    """
+    if omega == 0.0:
+        tau_new = 2.0 * tau
+        m_new = max(1, math.ceil(3 * m / 4))
+    else:
+        q = max(1.0, m / 4.0)
+        tau_new = tau * (omega / opts.gamma) ** (-1.0 / q)
+        tau_new = min(max(tau_new, tau / 5.0), 2.0 * tau)
+        dm = math.ceil(math.log(omega / opts.gamma) / math.log(opts.kappa))
+        m_new = m + dm
+        m_new = min(max(m_new, math.ceil(3 * m / 4)), m * 4 // 3 + 1)
+    m_new = max(1, min(m_new, opts.m_max, cap))
+    return tau_new, m_new
+
+
+def prefer_step_size(c_tau: float, c_m: float, accepted: bool, m_new: int, m: int) -> bool:
+    """Algorithm 1 step 5 (reading R8): True to update tau, False to update m.
+
+    The step size is updated when C(tau_new, m) <= C(tau, m_new), and after a
+    rejection whenever the Krylov size cannot change (m_new = m).
+    """
+    return c_tau <= c_m or (not accepted and m_new == m)
 
 
 class IOM2Basis:
@@ -233,8 +271,6 @@ def phipm_simul_iom2(Amul: Callable[[np.ndarray], np.ndarray],
                     Hm = basis.H[0:m_use, 0:m_use]
                     hnext = basis.H[m_use, m_use - 1]
                     hnorm = augmented_norm1(Hm, tau_k, p)
-                    if not hnorm <= HNORM_MAX:
-                        raise NoConvergence(f"phipm_simul_iom2: ||tau Hhat||_1 = {hnorm} beyond {HNORM_MAX}")
                     phi_p, phi_p1 = phi_krylov(Hm, tau_k, p)
                     eps = tau_k ** p * beta * tau_k * abs(hnext) * abs(phi_p1[m_use - 1])  # R6
                 else:
@@ -243,27 +279,17 @@ def phipm_simul_iom2(Amul: Callable[[np.ndarray], np.ndarray],
                 omega = t_out * eps / (tau_k * opts.tol * scale)
                 if not math.isfinite(omega):
                     raise NoConvergence("phipm_simul_iom2: non-finite error estimate")
-                accepted = omega <= opts.delta if rp is None else rec.accepted
+                accepted = accepts(omega, opts.delta) if rp is None else rec.accepted
                 stats.trace.append(Attempt(t=t, tau=tau_k, m=m_use, omega=omega, accepted=accepted))
                 stats.m_max_used = max(stats.m_max_used, m_use)
 
                 # steps 4-5: proposals and cost comparison (R8)
                 cap = basis.size if (basis is not None and basis.broken) else opts.m_max
-                if omega == 0.0:
-                    tau_new = 2.0 * tau_k
-                    m_new = max(1, math.ceil(3 * m_use / 4))
-                else:
-                    q = max(1.0, m_use / 4.0)
-                    tau_new = tau_k * (omega / opts.gamma) ** (-1.0 / q)
-                    tau_new = min(max(tau_new, tau_k / 5.0), 2.0 * tau_k)
-                    dm = math.ceil(math.log(omega / opts.gamma) / math.log(opts.kappa))
-                    m_new = m_use + dm
-                    m_new = min(max(m_new, math.ceil(3 * m_use / 4)), m_use * 4 // 3 + 1)
-                m_new = max(1, min(m_new, opts.m_max, cap))
+                tau_new, m_new = proposals(omega, tau_k, m_use, cap, opts)
                 hnorm_new = augmented_norm1(Hm, tau_new, p) if basis is not None else 1.0
                 c_tau = cost(tau_new, m_use, p, remaining, N, nA, hnorm_new)
                 c_m = cost(tau_k, m_new, p, remaining, N, nA, hnorm)
-                take_tau = c_tau <= c_m or (not accepted and m_new == m_use)
+                take_tau = prefer_step_size(c_tau, c_m, accepted, m_new, m_use)
 
                 if accepted:
                     # y_{k+1} = tau^p phi_p(tau A) w_p + sum_{j<p} tau^j/j! w_j (eq3.17, R2, R5)
