@@ -123,6 +123,14 @@ int swe_create_grid_host(int level, double radius, double g, double omega, doubl
  * the table's element count (error otherwise).  Names and layouts
  * (ncells = N_g, slot k = 0..5, component c = 0..2):
  *   "nbr"  int32  [6][N_g] neighbour of slot k (pentagons: slot 5 = the cell)
+ *   "gen"  int32  [N_g]    generation index of each cell: the permutation from
+ *                          the grid's order to the order refinement creates the
+ *                          nodes in (the 12 icosahedron nodes: north pole,
+ *                          northern ring at longitudes 2 pi k/5, southern ring
+ *                          at 2 pi k/5 + pi/5, south pole; then, per
+ *                          refinement, the new edge midpoints by ascending
+ *                          (smaller, larger) generation index of the edge's
+ *                          endpoints); cell i of the grid is node gen[i]
  *   "wl"   double [6][N_g] l_e/(d_e A_i);  "wld" double [N_g] -sum_k wl
  *   "nc"   double [3][6][N_g] edge-value weight x l_e nu_e/A_i of slot k
  *   "ndd"  double [3][N_g]    the same for the cell itself (D diagonal)
@@ -161,16 +169,20 @@ int swe_jv(const swe_grid* grid, const double* u, const double* x, double* jx, v
 
 /* jx = J(u) x like swe_jv, but without allocating any device memory.  The
  * paper has no counterpart: this exists for callers that may not allocate at
- * the time of the call (work enqueued during CUDA-graph stream capture, code
- * running under another framework's memory pool or a fixed device budget,
- * real-time loops), since swe_jv allocates the grid's workspace on first use.
- * Scratch is a static device array in the library image sized for grids of at
- * most 40962 cells (level 6; 3.9 MB held on every GPU that loads the
- * library); larger grids return SWE_ERR_INVALID_ARG.  The first call on each
- * device looks the array up (cudaGetSymbolAddress) with that device current
- * and should come before any stream capture.  All calls share the array:
+ * the time of the call (code running under another framework's memory pool
+ * or a fixed device budget reserved at start-up, real-time loops that cannot
+ * take an allocation's latency or failure), since swe_jv allocates the grid's
+ * workspace on first use.  Scratch is a static device array in the library
+ * image sized for grids of at most 40962 cells (level 6; 3.9 MB held on every
+ * GPU that loads the library until the process exits); larger grids return
+ * SWE_ERR_INVALID_ARG.  The first call on each device looks the array up
+ * (cudaGetSymbolAddress) with that device current and should come before any
+ * stream capture.  All calls share the array, which keeps what the last call
+ * wrote (every plane is written before it is read, so nothing is cleared):
  * calls that overlap on the GPU (e.g. on two streams) race and must be
- * serialised by the caller.  u, x, jx: device, n doubles; jx distinct. */
+ * serialised by the caller.  u, x, jx: device, n doubles; jx must not overlap
+ * u or x (SWE_ERR_INVALID_ARG); the grid's device must be current
+ * (SWE_ERR_INVALID_ARG otherwise). */
 int swe_jv_noalloc(const swe_grid* grid, const double* u, const double* x, double* jx, void* stream);
 
 /* Surface height h_s (Sec. 2: E = |u|^2/2 + g (h + h_s) in Eq. eq:sweqsinv):

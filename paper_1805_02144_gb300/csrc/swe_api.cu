@@ -986,9 +986,10 @@ int run_transposed(swe_grid* g, const double* u, const double* lam, double alpha
 
 // Accessors for the allocation-free entry point (swe_noalloc.cu).
 namespace swe {
-int grid_device_tables(const swe_grid* g, Tables* out) {
+int grid_device_tables(const swe_grid* g, Tables* out, int* device) {
   if (!g->dtab) return fail(SWE_ERR_INVALID_ARG, "grid was built on the host only");
   *out = g->T;
+  *device = g->device;
   return SWE_OK;
 }
 void set_last_error(const std::string& msg) { g_last_error = msg; }
@@ -1073,6 +1074,7 @@ int swe_grid_export(const swe_grid* g, const char* table, void* out, int64_t cou
   };
   std::string t(table);
   if (t == "nbr") return put(h.nbr.data(), h.nbr.size(), 4);
+  if (t == "gen") return put(h.gen.data(), h.gen.size(), 4);
   if (t == "wl") return put(h.wl.data(), h.wl.size(), 8);
   if (t == "wld") return put(h.wld.data(), h.wld.size(), 8);
   if (t == "nc") return put(h.nc.data(), h.nc.size(), 8);

@@ -4,12 +4,12 @@
 // eta / n x u planes of the linearisation state) inside the grid's workspace,
 // which the library allocates with cudaMalloc on first use (and that workspace
 // also holds the Krylov basis of phi_action).  Some callers must not allocate
-// device memory at that point: code that enqueues work while a stream is
-// being captured into a CUDA graph (allocation is not allowed inside a
-// capture), code that runs under another framework's memory pool or a fixed
-// device-memory budget reserved at start-up, and real-time loops that cannot
-// take an allocation's latency or an out-of-memory failure mid-run.  This
-// entry point uses a scratch array that is part of the library image instead.
+// device memory at that point: code that runs under another framework's
+// memory pool or under a fixed device-memory budget reserved at start-up
+// (a cudaMalloc behind the pool's back breaks its accounting or fails), and
+// real-time loops that cannot take an allocation's latency or an
+// out-of-memory failure in the middle of a run.  This entry point uses a
+// scratch array that is part of the library image instead.
 //
 // The scratch is one file-scope device array of kScratchDoubles doubles
 // (12 planes of up to kMaxCells cells: 3.9 MB), resident on every GPU that
@@ -21,6 +21,8 @@
 // example on two streams) race on it and must be serialised by the caller.
 #include <cuda_runtime.h>
 
+#include <stdint.h>
+
 #include <mutex>
 #include <string>
 
@@ -30,8 +32,9 @@
 using namespace swe;
 
 namespace swe {
-// Device tables of a grid handle (defined with the handle in swe_api.cu).
-int grid_device_tables(const swe_grid* g, Tables* out);
+// Device tables of a grid handle and the device they live on (defined with
+// the handle in swe_api.cu).
+int grid_device_tables(const swe_grid* g, Tables* out, int* device);
 void set_last_error(const std::string& msg);
 }  // namespace swe
 
@@ -65,14 +68,10 @@ __global__ void k_pass2_na(Tables T, const double* x, const double* tmp, const d
   }
 }
 
-// Device address of the scratch array on the current device (looked up once).
-int scratch_ptr(double** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) {
-    set_last_error(std::string("swe_jv_noalloc: cudaGetDevice: ") + cudaGetErrorString(e));
-    return SWE_ERR_CUDA;
-  }
+// Device address of the scratch array on device dev, which must be the
+// current device (looked up once per device).
+int scratch_ptr(int dev, double** out) {
+  cudaError_t e;
   if (dev < 0 || dev >= kMaxDevices) {
     set_last_error("swe_jv_noalloc: device ordinal out of range");
     return SWE_ERR_INVALID_ARG;
@@ -100,7 +99,8 @@ extern "C" int swe_jv_noalloc(const swe_grid* grid, const double* u, const doubl
     return SWE_ERR_INVALID_ARG;
   }
   Tables T;
-  int rc = grid_device_tables(grid, &T);
+  int grid_dev = -1;
+  int rc = grid_device_tables(grid, &T, &grid_dev);
   if (rc != SWE_OK) return rc;
   if (T.ng > kMaxCells) {
     set_last_error("swe_jv_noalloc: grid has " + std::to_string(T.ng) +
@@ -108,8 +108,32 @@ extern "C" int swe_jv_noalloc(const swe_grid* grid, const double* u, const doubl
                    " (level 6); use swe_jv for larger grids");
     return SWE_ERR_INVALID_ARG;
   }
+  // jx is written while neighbouring cells of x (and cell values of u) are
+  // still being read: the output must not overlap either input
+  const size_t nbytes = (size_t)4 * T.ng * sizeof(double);
+  auto overlaps = [nbytes](const void* a, const void* b) {
+    const uintptr_t pa = (uintptr_t)a, pb = (uintptr_t)b;
+    return pa < pb + nbytes && pb < pa + nbytes;
+  };
+  if (overlaps(jx, x) || overlaps(jx, u)) {
+    set_last_error("swe_jv_noalloc: jx must not overlap u or x");
+    return SWE_ERR_INVALID_ARG;
+  }
+  // the tables and the scratch belong to the grid's device: launching with
+  // another device current would read the grid's memory from the wrong GPU
+  int cur = -1;
+  cudaError_t ge = cudaGetDevice(&cur);
+  if (ge != cudaSuccess) {
+    set_last_error(std::string("swe_jv_noalloc: cudaGetDevice: ") + cudaGetErrorString(ge));
+    return SWE_ERR_CUDA;
+  }
+  if (cur != grid_dev) {
+    set_last_error("swe_jv_noalloc: the grid was built on device " + std::to_string(grid_dev) +
+                   " but device " + std::to_string(cur) + " is current");
+    return SWE_ERR_INVALID_ARG;
+  }
   double* scratch = nullptr;
-  if ((rc = scratch_ptr(&scratch)) != SWE_OK) return rc;
+  if ((rc = scratch_ptr(cur, &scratch)) != SWE_OK) return rc;
   double* tmp = scratch;                          // 8 planes of ng
   double* aux = scratch + (size_t)8 * T.ng;       // 4 planes of ng
   cudaStream_t st = (cudaStream_t)stream;
