@@ -69,10 +69,10 @@ class Grid:
     def export(self, table: str) -> np.ndarray:
         """Host copy of an operator table (see swe_grid_export), shaped [..., ncells]."""
         ng = self.ncells
-        shapes = {"nbr": (6, ng), "wl": (6, ng), "wld": (ng,), "nc": (3, 6, ng), "ndd": (3, ng),
+        shapes = {"nbr": (6, ng), "gen": (ng,), "wl": (6, ng), "wld": (ng,), "nc": (3, 6, ng), "ndd": (3, ng),
                   "sdg": (3, ng), "vc": (3, 6, ng), "vd": (3, ng), "wlT": (6, ng), "ncT": (3, 6, ng),
                   "vcT": (3, 6, ng)}
-        out = np.empty(shapes[table], dtype=np.int32 if table == "nbr" else np.float64)
+        out = np.empty(shapes[table], dtype=np.int32 if table in ("nbr", "gen") else np.float64)
         check(load().swe_grid_export(self.handle, table.encode(), out.ctypes.data_as(C.c_void_p),
                                      out.size))
         return out

@@ -90,9 +90,14 @@ void icosahedron(std::vector<V3>& p, std::vector<Tri>& t) {
   }
 }
 
-void refine(std::vector<V3>& p, std::vector<Tri>& t) {
+// One refinement.  gen[v] is the generation index of node v (see
+// build_host_grid); the new midpoints are numbered here in the order they are
+// first met, and their generation indices follow the ascending
+// (smaller, larger) generation indices of their parent edges.
+void refine(std::vector<V3>& p, std::vector<Tri>& t, std::vector<int32_t>& gen) {
   std::unordered_map<uint64_t, int> mid;
   mid.reserve(t.size() * 2);
+  std::vector<std::array<int32_t, 3>> parents;  // (lower gen, upper gen, node)
   auto midpoint = [&](int a, int b) {
     uint64_t k = ekey(a, b);
     auto it = mid.find(k);
@@ -100,6 +105,7 @@ void refine(std::vector<V3>& p, std::vector<Tri>& t) {
     int id = (int)p.size();
     p.push_back(unit(p[a] + p[b]));
     mid.emplace(k, id);
+    parents.push_back({std::min(gen[a], gen[b]), std::max(gen[a], gen[b]), id});
     return id;
   };
   std::vector<Tri> out;
@@ -113,6 +119,10 @@ void refine(std::vector<V3>& p, std::vector<Tri>& t) {
     out.push_back({{ab, bc, ca}});
   }
   t.swap(out);
+  const int32_t nv = (int32_t)gen.size();
+  std::sort(parents.begin(), parents.end());
+  gen.resize(p.size());
+  for (size_t r = 0; r < parents.size(); ++r) gen[parents[r][2]] = nv + (int32_t)r;
 }
 
 // Skilling's transpose form of the Hilbert index (J. Skilling, "Programming
@@ -153,7 +163,12 @@ int build_host_grid(int level, double radius, bool reorder, HostGrid& g, const c
   std::vector<V3> P;
   std::vector<Tri> T;
   icosahedron(P, T);
-  for (int l = 0; l < level; ++l) refine(P, T);
+  // generation index: the 12 icosahedron nodes in the order above, then per
+  // refinement the new midpoints by ascending (smaller, larger) generation
+  // index of the edge they split
+  std::vector<int32_t> gen(P.size());
+  std::iota(gen.begin(), gen.end(), 0);
+  for (int l = 0; l < level; ++l) refine(P, T, gen);
   const int ng = (int)P.size();
   const int nt = (int)T.size();
 
@@ -325,8 +340,10 @@ int build_host_grid(int level, double radius, bool reorder, HostGrid& g, const c
   g.ndd.assign((size_t)3 * ng, 0.0);
   g.sdg.assign((size_t)3 * ng, 0.0);
   g.vd.assign((size_t)3 * ng, 0.0);
+  g.gen.assign(ng, 0);
   for (int ni = 0; ni < ng; ++ni) {
     int i = perm[ni];
+    g.gen[ni] = gen[i];
     g.xyz[ni] = P[i].x;
     g.xyz[(size_t)ng + ni] = P[i].y;
     g.xyz[(size_t)2 * ng + ni] = P[i].z;

@@ -25,6 +25,8 @@ struct HostGrid {
   std::vector<double> vc;           // [3][6][ng] edge-value weights x l_e t_e / A_i
   std::vector<double> vd;           // [3][ng]    self weight of the same
   int64_t nA = 0;                   // structural nonzeros of J
+  std::vector<int32_t> gen;         // [ng] generation index of each cell (the
+                                    // order nodes are created by refinement)
   // transposed slot tables: cell j, slot k (neighbour i = nbr[k][j]) holds
   // row i's coefficient for column j (diagonals are unchanged by transposition)
   std::vector<double> wlT;          // [6][ng]

@@ -137,3 +137,21 @@ def test_host_grid_rejects_compute_and_bad_arguments(lib):
     h = C.c_void_p()
     assert lib.swe_create_grid_host(11, 6.4e6, 9.8, 7e-5, 4e-4, 1, C.byref(h)) == -1
     assert lib.swe_create_grid_host(2, -1.0, 9.8, 7e-5, 4e-4, 1, C.byref(h)) == -1
+
+
+@pytest.mark.parametrize("lev", [0, 1, 2, 4, 6])
+def test_generation_index_is_the_oracle_order(lib, lev):
+    """The exported generation index maps the grid's cells to the order in
+    which refinement creates the nodes: it is a permutation and picks the
+    oracle's node (built in that order) at the same position."""
+    from paper_1805_02144_gb300.api import Grid
+    from oracle.mesh import build_grid
+    G = Grid(lev, host_only=True)
+    gen = G.export("gen")
+    assert np.array_equal(np.sort(gen), np.arange(G.ncells))
+    og = build_grid(lev)
+    assert np.abs(og.x[gen] - G.cell_centres()).max() < 1e-14
+    # without reordering the grid is in generation order up to the midpoint
+    # numbering of each refinement; the first 12 cells are the icosahedron
+    H = Grid(lev, host_only=True, reorder=False)
+    assert np.array_equal(H.export("gen")[:12], np.arange(12))
