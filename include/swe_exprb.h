@@ -316,12 +316,21 @@ int swe_profile_read(swe_grid* grid, swe_profile* out, void* stream);
  * and Krylov workspace.  Member states are library-owned device buffers
  * (n_m doubles, grid order); set/get copy device to device.  A run enqueues
  * two memsets and one kernel and allocates nothing, so it can be captured in
- * a CUDA graph.  The block split starts from a work model (cells x 2^level x
- * simulated time); swe_ensemble_tune runs the ensemble `rounds` times (then
- * restores the states and the carried Krylov sizes), fits each member's group
- * time as serial + parallel / blocks from its last two runs, re-splits to
- * minimise the predicted longest group, and finally keeps the split whose
- * measured longest group was shortest (3 or more rounds use the fit).
+ * a CUDA graph.  A group of blocks may hold several members, which then run
+ * one after the other on those blocks (small members stacked, so that they
+ * share blocks instead of idling on one each).  The launch starts with
+ * 96-thread blocks (4 per SM), one member per group and a block split from a
+ * work model (cells x 2^level x simulated time).  swe_ensemble_tune is the
+ * autotuner: for each launch shape (96 x 4, 128 x 3, 192 x 2 and 384 x 1
+ * threads x blocks per SM, which set how finely blocks, and so cells per
+ * thread, can be divided between members) it runs the ensemble `rounds`
+ * times, fits each member's time as serial + parallel / blocks from its last
+ * two runs (carried to the next shape scaled by its block size), re-plans the
+ * groups (stacking members that would take at most half the longest group's
+ * time on one block) and the split that minimises the predicted longest
+ * group, and finally keeps the shape, groups and split whose measured longest
+ * group was shortest; it restores the states and carried Krylov sizes after
+ * every run.  swe_ensemble_shape reports the launch in use.
  * Each member carries its last accepted Krylov size per call from step to
  * step and from run to run (m carry);
  * swe_ensemble_reset clears it, as for a new trajectory.
@@ -338,10 +347,22 @@ int swe_ensemble_run(swe_ensemble* ens, void* stream);
 int swe_ensemble_reset(swe_ensemble* ens, void* stream);
 int swe_ensemble_tune(swe_ensemble* ens, int rounds, void* stream);
 /* Waits for `stream`; per-member statistics of the last run (array of nmem,
- * or NULL; trace not filled), each member's group time in ms (or NULL) and
- * its block count (or NULL). */
+ * or NULL; trace not filled), each member's own time in ms (or NULL; from its
+ * start to its end on its group's blocks) and its group's block count (or
+ * NULL). */
 int swe_ensemble_stats(swe_ensemble* ens, phi_stats* stats, double* member_ms, int* member_blocks,
                        void* stream);
+/* The launch in use: threads per block, resident blocks per SM, blocks
+ * launched, the number of member groups and, in member_group (nmem ints),
+ * each member's group; groups run their members in ascending order (any
+ * output may be NULL). */
+int swe_ensemble_shape(const swe_ensemble* ens, int* threads, int* blocks_per_sm, int* nblocks, int* ngroups,
+                       int* member_group);
+/* Waits for `stream`; *flop = the algorithmic FP64 operation count of the
+ * last run (per cell: 342 per IOM2 column, 310 per w_j product, 8 per
+ * substep-combination term, the counts swe_profile reports for phi_action),
+ * summed over members. */
+int swe_ensemble_work(swe_ensemble* ens, double* flop, void* stream);
 
 /* Self-test of the failure path of every device-side wait: one block whose
  * thread 0 polls, exactly as the grid barriers do, a flag that nothing sets.

@@ -28,7 +28,7 @@ EXPORTS = ["swe_phi_opts_default", "swe_create_grid", "swe_create_grid_host", "s
            "exprb_step", "exprb_step_adjoint", "swe_profile_enable", "swe_profile_read", "swe_device_status",
            "swe_last_error", "swe_ensemble_create", "swe_ensemble_destroy", "swe_ensemble_set_state",
            "swe_ensemble_get_state", "swe_ensemble_run", "swe_ensemble_reset", "swe_ensemble_tune",
-           "swe_ensemble_stats", "swe_selftest_wait"]
+           "swe_ensemble_stats", "swe_ensemble_shape", "swe_ensemble_work", "swe_selftest_wait"]
 
 
 class PhiOptsC(C.Structure):
@@ -122,6 +122,9 @@ def load(path: Optional[str] = None) -> C.CDLL:
     L.swe_ensemble_reset.argtypes = [vp, vp]
     L.swe_ensemble_tune.argtypes = [vp, C.c_int, vp]
     L.swe_ensemble_stats.argtypes = [vp, C.POINTER(PhiStatsC), dp, C.POINTER(C.c_int), vp]
+    ip = C.POINTER(C.c_int)
+    L.swe_ensemble_shape.argtypes = [vp, ip, ip, ip, ip, ip]
+    L.swe_ensemble_work.argtypes = [vp, dp, vp]
     L.swe_last_error.argtypes = []
     L.swe_last_error.restype = C.c_char_p
     for name in ("swe_create_grid", "swe_create_grid_host", "swe_grid_export", "swe_grid_query", "swe_grid_cell_centres", "swe_grid_cell_areas",
@@ -130,7 +133,7 @@ def load(path: Optional[str] = None) -> C.CDLL:
                  "swe_scheme_state_reset", "exprb_step", "exprb_step_adjoint", "swe_device_status", "swe_profile_enable",
                  "swe_profile_read", "swe_ensemble_create", "swe_ensemble_set_state",
                  "swe_ensemble_get_state", "swe_ensemble_run", "swe_ensemble_reset", "swe_ensemble_tune",
-                 "swe_ensemble_stats", "swe_selftest_wait"):
+                 "swe_ensemble_stats", "swe_ensemble_shape", "swe_ensemble_work", "swe_selftest_wait"):
         getattr(L, name).restype = C.c_int
     _LIB = L
     return L

@@ -372,6 +372,21 @@ class Ensemble:
         return {"status": [st[i].status for i in range(nm)], "n_jv": [st[i].n_jv for i in range(nm)],
                 "member_ms": [ms[i] for i in range(nm)], "blocks": [nb[i] for i in range(nm)]}
 
+    def shape(self) -> dict:
+        """The launch in use: threads per block, blocks per SM, blocks launched,
+        number of member groups and each member's group."""
+        t, per, nb, ng = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+        mg = (C.c_int * self.nmem)()
+        check(load().swe_ensemble_shape(self.handle, C.byref(t), C.byref(per), C.byref(nb), C.byref(ng), mg))
+        return {"threads": t.value, "blocks_per_sm": per.value, "nblocks": nb.value, "groups": ng.value,
+                "member_group": [mg[i] for i in range(self.nmem)]}
+
+    def work(self, stream=None) -> float:
+        """Algorithmic FP64 operations of the last run."""
+        f = C.c_double()
+        check(load().swe_ensemble_work(self.handle, C.byref(f), _stream(stream)))
+        return f.value
+
     def close(self) -> None:
         if self.handle:
             load().swe_ensemble_destroy(self.handle)

@@ -14,6 +14,7 @@ constexpr int NRED = 8;    // values per grid reduction
 // Statistics accumulated on the device over one phi_action or one exprb_step.
 struct DevStats {
   int n_jv, n_sub, n_rej, m_last, m_max_used, status, n_trace, pad;
+  long long n_iter, n_wjv, comb_terms;  // IOM2 columns, w_j products, combination terms
 };
 
 // Operation counters accumulated while profiling is on.
@@ -121,6 +122,14 @@ struct PhiArgsT {
 using PhiArgs = PhiArgsT<double>;
 using PhiArgsF = PhiArgsT<float>;
 
+constexpr int ENS_SHAPES = 4;  // launch shapes of the ensemble kernel (96x4, 128x3, 192x2, 384x1)
+
+// Algorithmic FP64 operations per cell (FMA = 2), counted from the stencils:
+// one IOM2 column (pass 1 + pass 2 of J x, two window dots, the
+// orthogonalisation and its norm), one w_j product (J x and the combination
+// of Eq. eq3.18), one term of the substep combination (Eq. eq3.17).
+constexpr double kFlopIter = 342.0, kFlopWjv = 310.0, kFlopComb = 8.0;
+
 // One member of an ensemble launch: an exprb42 trajectory (Eq. eq3.11 with
 // the two phipm_simul_iom2 calls of Sec. 4.4) advanced nsteps steps by the
 // group of blocks [b0, b0 + nb).
@@ -137,7 +146,9 @@ struct EnsMember {
   double dt;
   int nsteps;
   int b0, nb;
-  unsigned long long t0, t1;  // globaltimer at the group's start and end (block 0)
+  int next;                   // the member that runs next on the same blocks, or -1
+  int pad;
+  unsigned long long t0, t1;  // globaltimer at the member's start and end (block 0)
 };
 
 }  // namespace swe

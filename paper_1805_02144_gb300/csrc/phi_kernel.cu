@@ -894,6 +894,9 @@ __device__ void phi_finish(const PhiArgsT<R>& a, Shared& sh) {
     int ab = ld_volatile_int(&a.sync->abort);
     int st = C->status != SWE_OK ? C->status : ab;
     S->n_jv += C->n_jv;
+    S->n_iter += C->n_iter;
+    S->n_wjv += C->n_wjv;
+    S->comb_terms += C->comb_terms;
     S->n_sub += C->n_sub;
     S->n_rej += C->n_rej;
     S->m_last = C->m_last;
@@ -908,7 +911,7 @@ __device__ void phi_finish(const PhiArgsT<R>& a, Shared& sh) {
       a.prof->wjv += C->n_wjv;
       a.prof->comb_terms += C->comb_terms;
       a.prof->launches += 1;
-      a.prof->flop += cells * (342.0 * C->n_iter + 310.0 * C->n_wjv + 8.0 * C->comb_terms);
+      a.prof->flop += cells * (kFlopIter * C->n_iter + kFlopWjv * C->n_wjv + kFlopComb * C->comb_terms);
       a.prof->bytes += cells * esz * (136.0 * C->n_iter + 104.0 * C->n_wjv + 32.0 * C->comb_terms);
       // tables: a pass 1 and a pass 2 per IOM2 iteration and per w_j product
       a.prof->table_bytes += cells * (62.0 * sizeof(R) + 48.0) * (double)(C->n_iter + C->n_wjv);
@@ -921,11 +924,10 @@ __device__ void phi_finish(const PhiArgsT<R>& a, Shared& sh) {
 // trajectory (stage passes, both phipm_simul_iom2 calls and the update) for
 // nsteps steps.  Members never wait on one another; each group has its own
 // barrier, control block and reduction buffer, so a member that stops (error)
-// does not hold the others.
+// does not hold the others.  A group may hold several members, run one after
+// the other on the same blocks (small members stacked so that they share
+// blocks instead of idling on one each).
 // ---------------------------------------------------------------------------
-constexpr int ENS_THREADS = 96;
-constexpr int ENS_MIN_BLOCKS = 4;
-
 __device__ bool ens_step(const EnsMember& M, Shared& sh) {
   const Tables& T = M.c1.T;
   const int ng = T.ng;
@@ -976,37 +978,58 @@ __device__ bool ens_step(const EnsMember& M, Shared& sh) {
   return grid_barrier(M.c1, sh, PH_PROLOGUE);
 }
 
-__global__ void __launch_bounds__(ENS_THREADS, ENS_MIN_BLOCKS)
-    ens_kernel(EnsMember* __restrict__ mem, const int* __restrict__ blk2mem) {
+template <int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) ens_kernel(EnsMember* __restrict__ mem, const int* __restrict__ blk2mem) {
   __shared__ Shared sh;
-  const int m = blk2mem[blockIdx.x];
-  EnsMember& M = mem[m];
-  if (threadIdx.x == 0) {
-    sh.gb = blockIdx.x - M.b0;
-    sh.gn = M.nb;
-    if (sh.gb == 0) M.t0 = globaltimer();
+  for (int m = blk2mem[blockIdx.x]; m >= 0; m = mem[m].next) {
+    EnsMember& M = mem[m];
+    if (threadIdx.x == 0) {
+      sh.gb = blockIdx.x - M.b0;
+      sh.gn = M.nb;
+      if (sh.gb == 0) M.t0 = globaltimer();
+    }
+    __syncthreads();
+    for (int s = 0; s < M.nsteps; ++s)
+      if (!ens_step(M, sh)) break;
+    if (threadIdx.x == 0 && sh.gb == 0) M.t1 = globaltimer();
+    __syncthreads();
   }
-  __syncthreads();
-  for (int s = 0; s < M.nsteps; ++s)
-    if (!ens_step(M, sh)) break;
-  if (threadIdx.x == 0 && sh.gb == 0) M.t1 = globaltimer();
 }
 
-int ens_max_blocks(int* nblocks, int* threads) {
+// Launch shapes of the ensemble kernel: block size x resident blocks per SM
+// (the same 384 threads per SM, 168 registers each); the block size sets the
+// granularity of the split between members.
+struct EnsVariant {
+  const void* fn;
+  int threads;
+};
+static const EnsVariant kEnsVariants[ENS_SHAPES] = {
+    {(const void*)ens_kernel<96, 4>, 96},
+    {(const void*)ens_kernel<128, 3>, 128},
+    {(const void*)ens_kernel<192, 2>, 192},
+    {(const void*)ens_kernel<384, 1>, 384},
+};
+
+int ens_max_blocks(int shape, int* nblocks, int* threads, int* per_sm) {
+  if (shape < 0 || shape >= ENS_SHAPES) return -1;
   int dev = 0, nsm = 0, per = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return -1;
   if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -1;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, ens_kernel, ENS_THREADS, 0) != cudaSuccess || per < 1)
+  const EnsVariant& v = kEnsVariants[shape];
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, v.fn, v.threads, 0) != cudaSuccess || per < 1)
     return -1;
   *nblocks = per * nsm;
-  *threads = ENS_THREADS;
+  *threads = v.threads;
+  if (per_sm) *per_sm = per;
   return 0;
 }
 
-int launch_ens_kernel(EnsMember* mem, const int* blk2mem, int nblocks, cudaStream_t stream) {
+int launch_ens_kernel(int shape, EnsMember* mem, const int* blk2mem, int nblocks, cudaStream_t stream) {
+  if (shape < 0 || shape >= ENS_SHAPES) return (int)cudaErrorInvalidValue;
+  const EnsVariant& v = kEnsVariants[shape];
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(nblocks);
-  cfg.blockDim = dim3(ENS_THREADS);
+  cfg.blockDim = dim3(v.threads);
   cfg.stream = stream;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;
@@ -1014,7 +1037,7 @@ int launch_ens_kernel(EnsMember* mem, const int* blk2mem, int nblocks, cudaStrea
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   void* args[] = {(void*)&mem, (void*)&blk2mem};
-  cudaError_t e = cudaLaunchKernelExC(&cfg, (const void*)ens_kernel, args);
+  cudaError_t e = cudaLaunchKernelExC(&cfg, v.fn, args);
   return e == cudaSuccess ? 0 : (int)e;
 }
 

@@ -24,8 +24,8 @@ int launch_adj_kernel(const AdjArgs& a, int nblocks, cudaStream_t st);
 template <class A>
 int launch_phi_kernel(const PhiLaunch& L, const A& a, cudaStream_t stream);
 int phi_select(int ng, int single, PhiLaunch* out);
-int ens_max_blocks(int* nblocks, int* threads);
-int launch_ens_kernel(EnsMember* mem, const int* blk2mem, int nblocks, cudaStream_t stream);
+int ens_max_blocks(int shape, int* nblocks, int* threads, int* per_sm);
+int launch_ens_kernel(int shape, EnsMember* mem, const int* blk2mem, int nblocks, cudaStream_t stream);
 }  // namespace swe
 
 using namespace swe;
@@ -115,10 +115,15 @@ struct swe_grid {
 
 struct swe_ensemble {
   int nmem = 0;
+  int shape = 0;              // launch shape (index of the ensemble kernel variant)
   int nblocks = 0;            // blocks of the launch (all co-resident)
+  int nb_alloc = 0;           // the most blocks any shape launches (sizes dblk, part)
   std::vector<swe_grid*> grids;
   std::vector<EnsMember> hmem;
-  std::vector<int> nb;        // blocks per member
+  std::vector<std::vector<int>> groups;  // members run back to back on one group of blocks
+  std::vector<int> gnb;       // blocks per group
+  std::vector<int> nb;        // blocks per member (its group's)
+  std::vector<double> weight; // work model per member (cells x 2^level x simulated time)
   EnsMember* dmem = nullptr;
   int* dblk = nullptr;        // block -> member
   GridSync* dsync = nullptr;  // nmem
@@ -1603,14 +1608,23 @@ int exprb_step_adjoint(swe_grid* g, int scheme, double dt, const double* u_n, co
 // ---------------------------------------------------------------------------
 static int ens_upload_split(swe_ensemble* E) {
   int b = 0;
-  std::vector<int> blk(E->nblocks, 0);
-  for (int m = 0; m < E->nmem; ++m) {
-    E->hmem[m].b0 = b;
-    E->hmem[m].nb = E->nb[m];
-    for (int k = 0; k < E->nb[m]; ++k) blk[b + k] = m;
-    b += E->nb[m];
+  std::vector<int> blk(E->nb_alloc, -1);
+  E->nb.assign(E->nmem, 0);
+  for (size_t g = 0; g < E->groups.size(); ++g) {
+    const std::vector<int>& mem = E->groups[g];
+    const int nbg = E->gnb[g];
+    if (mem.empty() || nbg < 1) return fail(SWE_ERR_INVALID_ARG, "ensemble: empty group");
+    if (b + nbg > E->nblocks) return fail(SWE_ERR_INVALID_ARG, "ensemble block split exceeds the launch");
+    for (size_t k = 0; k < mem.size(); ++k) {
+      EnsMember& M = E->hmem[mem[k]];
+      M.b0 = b;
+      M.nb = nbg;
+      M.next = k + 1 < mem.size() ? mem[k + 1] : -1;
+      E->nb[mem[k]] = nbg;
+    }
+    for (int k = 0; k < nbg; ++k) blk[b + k] = mem[0];
+    b += nbg;
   }
-  if (b > E->nblocks) return fail(SWE_ERR_INVALID_ARG, "ensemble block split exceeds the launch");
   E->nblocks = b;
   CK(cudaMemcpy(E->dblk, blk.data(), (size_t)b * sizeof(int), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(E->dmem, E->hmem.data(), E->hmem.size() * sizeof(EnsMember), cudaMemcpyHostToDevice));
@@ -1693,16 +1707,22 @@ extern "C" int swe_ensemble_create(swe_grid* const* grids, int nmem, const doubl
   if (rc) return rc;
   if (o.precision != 0 || o.replay || o.iom != 2)
     return fail(SWE_ERR_INVALID_ARG, "ensemble: FP64, IOM2, without replay only");
-  int NB = 0, threads = 0;
-  if (ens_max_blocks(&NB, &threads) != 0) return fail(SWE_ERR_CUDA, "ensemble: occupancy query failed");
+  int NB = 0, threads = 0, nb_alloc = 0;
+  if (ens_max_blocks(0, &NB, &threads, nullptr) != 0) return fail(SWE_ERR_CUDA, "ensemble: occupancy query failed");
   if (nmem > NB) return fail(SWE_ERR_INVALID_ARG, "ensemble: more members than co-resident blocks");
+  for (int sh = 0; sh < ENS_SHAPES; ++sh) {
+    int nbs = 0, ts = 0;
+    if (ens_max_blocks(sh, &nbs, &ts, nullptr) == 0) nb_alloc = std::max(nb_alloc, nbs);
+  }
   for (int m = 0; m < nmem; ++m) {
     if (!grids[m] || !grids[m]->dtab || !(dt[m] > 0.0) || nsteps[m] < 0)
       return fail(SWE_ERR_INVALID_ARG, "ensemble: each member needs a device grid, dt > 0, nsteps >= 0");
   }
   std::unique_ptr<swe_ensemble> E(new swe_ensemble());
   E->nmem = nmem;
+  E->shape = 0;
   E->nblocks = NB;
+  E->nb_alloc = nb_alloc;
   E->grids.assign(grids, grids + nmem);
   // workspace layout per member (doubles): Vbuf (KMAX+1)n, W (PMAX+1)n, tmp 8ng, Lring 3n,
   // Zbuf n, aux 4ng, part NB*NRED, u n, vF n, v3 n, y1 n, w n, tmpS 8ng  + ctrl, slots
@@ -1713,7 +1733,7 @@ extern "C" int swe_ensemble_create(swe_grid* const* grids, int nmem, const doubl
     const size_t ng = grids[m]->T.ng, n = 4 * ng;
     off[m] = total;
     size_t d = (size_t)(KMAX + 1) * n + (size_t)(PMAX + 1) * n + 8 * ng + 3 * n + n + 4 * ng +
-               (size_t)NB * NRED + 5 * n + 8 * ng;
+               (size_t)nb_alloc * NRED + 5 * n + 8 * ng;
     total += al(d * 8) + al(sizeof(PhiCtrl));
   }
   size_t nstates = 0;
@@ -1723,7 +1743,7 @@ extern "C" int swe_ensemble_create(swe_grid* const* grids, int nmem, const doubl
   }
   cudaError_t e = cudaMalloc(&E->dws, total);
   if (e == cudaSuccess) e = cudaMalloc(&E->dmem, (size_t)nmem * sizeof(EnsMember));
-  if (e == cudaSuccess) e = cudaMalloc(&E->dblk, (size_t)NB * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&E->dblk, (size_t)nb_alloc * sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&E->dsync, (size_t)nmem * sizeof(GridSync));
   if (e == cudaSuccess) e = cudaMalloc(&E->dstats, (size_t)nmem * sizeof(DevStats));
   if (e == cudaSuccess) e = cudaMalloc(&E->backup, nstates * sizeof(double));
@@ -1757,7 +1777,7 @@ extern "C" int swe_ensemble_create(swe_grid* const* grids, int nmem, const doubl
     double* Lring = take(3 * n);
     double* Zbuf = take(n);
     double* aux = take(4 * ng);
-    double* part = take((size_t)NB * NRED);
+    double* part = take((size_t)nb_alloc * NRED);
     M.u = take(n);
     M.vF = take(n);
     M.v3 = take(n);
@@ -1766,7 +1786,7 @@ extern "C" int swe_ensemble_create(swe_grid* const* grids, int nmem, const doubl
     M.tmpS = take(8 * ng);
     M.aux = aux;
     char* q = (char*)E->dws + off[m] + al(((size_t)(KMAX + 1) * n + (size_t)(PMAX + 1) * n + 8 * ng + 3 * n +
-                                             n + 4 * ng + (size_t)NB * NRED + 5 * n + 8 * ng) * 8);
+                                             n + 4 * ng + (size_t)nb_alloc * NRED + 5 * n + 8 * ng) * 8);
     PhiCtrl* ctrl = (PhiCtrl*)q;
     int* slots = E->dslots + 2 * m;
     M.dt = dt[m];
@@ -1819,7 +1839,10 @@ extern "C" int swe_ensemble_create(swe_grid* const* grids, int nmem, const doubl
     // i.e. with 2^level * (simulated time); cost per iteration with cells
     weight[m] = (double)ng * std::pow(2.0, g->host.level) * dt[m] * (nsteps[m] > 0 ? nsteps[m] : 0) + 1.0;
   }
-  E->nb = ens_split(weight, NB);
+  E->weight = weight;
+  E->groups.clear();
+  for (int m = 0; m < nmem; ++m) E->groups.push_back({m});
+  E->gnb = ens_split(weight, NB);
   if ((rc = ens_upload_split(E.get()))) {
     swe_ensemble_destroy(E.release());
     return rc;
@@ -1866,7 +1889,7 @@ extern "C" int swe_ensemble_run(swe_ensemble* E, void* stream) {
   cudaStream_t st = S(stream);
   CK(cudaMemsetAsync(E->dsync, 0, (size_t)E->nmem * sizeof(GridSync), st));
   CK(cudaMemsetAsync(E->dstats, 0, (size_t)E->nmem * sizeof(DevStats), st));
-  int e = launch_ens_kernel(E->dmem, E->dblk, E->nblocks, st);
+  int e = launch_ens_kernel(E->shape, E->dmem, E->dblk, E->nblocks, st);
   if (e != 0) return cuda_fail((cudaError_t)e, "cudaLaunchKernelEx(ens_kernel)");
   return SWE_OK;
 }
@@ -1895,63 +1918,185 @@ extern "C" int swe_ensemble_stats(swe_ensemble* E, phi_stats* stats, double* mem
   return SWE_OK;
 }
 
+// Groups and blocks for `total` blocks from per-member fits t_m(b) = s_m +
+// p_m / b [ms] (members of a group run one after the other on its blocks, so
+// a group takes sum s + (sum p) / b).  Starting from one member per group and
+// the split that minimises the predicted longest group (time T), members that
+// would take at most T/2 on one block are stacked, longest first, into the
+// first group whose one-block time stays within T; the freed blocks are
+// split again.  Repeated while the predicted longest group gets shorter.
+static void ens_plan(const std::vector<double>& s, const std::vector<double>& p, int total,
+                     std::vector<std::vector<int>>& groups, std::vector<int>& gnb) {
+  const int n = (int)s.size();
+  auto split = [&](const std::vector<std::vector<int>>& gr, std::vector<int>& nb) {
+    std::vector<double> sg(gr.size(), 0.0), pg(gr.size(), 0.0);
+    for (size_t g = 0; g < gr.size(); ++g)
+      for (int m : gr[g]) {
+        sg[g] += s[m];
+        pg[g] += p[m];
+      }
+    nb = ens_split_model(sg, pg, total);
+    double T = 0.0;
+    for (size_t g = 0; g < gr.size(); ++g) T = std::max(T, sg[g] + pg[g] / nb[g]);
+    return T;
+  };
+  groups.clear();
+  for (int m = 0; m < n; ++m) groups.push_back({m});
+  double T = split(groups, gnb);
+  for (int pass = 0; pass < 4; ++pass) {
+    std::vector<int> small, big;
+    for (int m = 0; m < n; ++m) (s[m] + p[m] <= 0.5 * T ? small : big).push_back(m);
+    std::sort(small.begin(), small.end(), [&](int a, int b) { return s[a] + p[a] > s[b] + p[b]; });
+    std::vector<std::vector<int>> bins;
+    std::vector<double> load;
+    for (int m : small) {
+      const double t1 = s[m] + p[m];
+      size_t k = 0;
+      while (k < bins.size() && load[k] + t1 > T) ++k;
+      if (k == bins.size()) {
+        bins.push_back({});
+        load.push_back(0.0);
+      }
+      bins[k].push_back(m);
+      load[k] += t1;
+    }
+    std::vector<std::vector<int>> cand = bins;
+    for (int m : big) cand.push_back({m});
+    if ((int)cand.size() > total || cand.size() == groups.size()) break;
+    std::vector<int> nb;
+    const double Tn = split(cand, nb);
+    if (!(Tn < T)) break;
+    groups = cand;
+    gnb = nb;
+    T = Tn;
+  }
+}
+
 extern "C" int swe_ensemble_tune(swe_ensemble* E, int rounds, void* stream) {
   if (!E || rounds < 0) return fail(SWE_ERR_INVALID_ARG, "ensemble_tune: bad arguments");
+  if (rounds == 0) return SWE_OK;
   cudaStream_t st = S(stream);
   for (int m = 0; m < E->nmem; ++m)
     CK(cudaMemcpyAsync(E->backup + E->state_off[m], E->hmem[m].u, (size_t)4 * E->grids[m]->T.ng * sizeof(double),
                        cudaMemcpyDeviceToDevice, st));
   CK(cudaMemcpyAsync(E->dslots_backup, E->dslots, (size_t)2 * E->nmem * sizeof(int), cudaMemcpyDeviceToDevice, st));
-  const int NB = std::accumulate(E->nb.begin(), E->nb.end(), 0);
-  // per member: the last two (blocks, ms) measurements, to fit ms = s + p / blocks
-  std::vector<std::pair<int, double>> last1(E->nmem, {0, 0.0}), last2(E->nmem, {0, 0.0});
-  std::vector<int> best_nb = E->nb;
+  const int nm = E->nmem;
+  int best_shape = E->shape, best_nblocks = E->nblocks;
+  std::vector<std::vector<int>> best_groups = E->groups;
+  std::vector<int> best_gnb = E->gnb;
   double best_t = -1.0;
-  for (int r = 0; r < rounds; ++r) {
-    int rc = swe_ensemble_run(E, stream);
-    if (rc) return rc;
-    std::vector<double> ms(E->nmem);
-    std::vector<phi_stats> ps(E->nmem);
-    if ((rc = swe_ensemble_stats(E, ps.data(), ms.data(), nullptr, stream))) return rc;
-    for (int m = 0; m < E->nmem; ++m)
-      if (ps[m].status != SWE_OK) return fail(ps[m].status, "ensemble_tune: a member failed");
-    const double tmax = *std::max_element(ms.begin(), ms.end());
-    if (best_t < 0.0 || tmax < best_t) {
-      best_t = tmax;
-      best_nb = E->nb;
-    }
-    std::vector<double> sv(E->nmem), pv(E->nmem);
-    for (int m = 0; m < E->nmem; ++m) {
-      last2[m] = last1[m];
-      last1[m] = {E->nb[m], ms[m]};
-      double sm = 0.0, pm = ms[m] * E->nb[m];  // one measurement: all parallel
-      const int b1 = last1[m].first, b2 = last2[m].first;
-      if (b2 > 0 && b2 != b1) {
-        const double t1 = last1[m].second, t2 = last2[m].second;
-        const double x1 = 1.0 / b1, x2 = 1.0 / b2;
-        const double pf = (t1 - t2) / (x1 - x2);
-        const double sf = t1 - pf * x1;
-        if (pf > 0.0 && sf >= 0.0) {
-          sm = sf;
-          pm = pf;
-        }
-      }
-      sv[m] = sm;
-      pv[m] = pm;
-    }
-    E->nb = ens_split_model(sv, pv, NB);
+  // fits t = s + p / b per member; p is carried between shapes in thread-blocks
+  // (p x threads), s as it is
+  std::vector<double> fs(nm, 0.0), fpt(nm, 0.0);
+  bool have_fit = false;
+  for (int sh = 0; sh < ENS_SHAPES; ++sh) {
+    int NB = 0, threads = 0;
+    if (ens_max_blocks(sh, &NB, &threads, nullptr) != 0 || NB < 1) continue;
+    E->shape = sh;
     E->nblocks = NB;
-    for (int m = 0; m < E->nmem; ++m)
-      CK(cudaMemcpyAsync(E->hmem[m].u, E->backup + E->state_off[m], (size_t)4 * E->grids[m]->T.ng * sizeof(double),
-                         cudaMemcpyDeviceToDevice, st));
-    CK(cudaMemcpyAsync(E->dslots, E->dslots_backup, (size_t)2 * E->nmem * sizeof(int), cudaMemcpyDeviceToDevice, st));
-    CK(cudaStreamSynchronize(st));
-    if ((rc = ens_upload_split(E))) return rc;
+    std::vector<double> sv(nm), pv(nm);
+    if (have_fit) {
+      for (int m = 0; m < nm; ++m) {
+        sv[m] = fs[m];
+        pv[m] = fpt[m] / threads;
+      }
+      ens_plan(sv, pv, NB, E->groups, E->gnb);
+    } else {
+      E->groups.clear();
+      for (int m = 0; m < nm; ++m) E->groups.push_back({m});
+      if (NB < nm) continue;
+      E->gnb = ens_split(E->weight, NB);
+    }
+    if ((int)E->groups.size() > NB) continue;
+    // per member: the last two (blocks, ms) measurements of this shape
+    std::vector<std::pair<int, double>> last1(nm, {0, 0.0}), last2(nm, {0, 0.0});
+    for (int r = 0; r < rounds; ++r) {
+      E->nblocks = NB;
+      int rc = ens_upload_split(E);
+      if (rc) return rc;
+      if ((rc = swe_ensemble_run(E, stream))) return rc;
+      std::vector<phi_stats> ps(nm);
+      std::vector<double> ms(nm);
+      if ((rc = swe_ensemble_stats(E, ps.data(), ms.data(), nullptr, stream))) return rc;
+      for (int m = 0; m < nm; ++m)
+        if (ps[m].status != SWE_OK) return fail(ps[m].status, "ensemble_tune: a member failed");
+      std::vector<EnsMember> hm(nm);
+      CK(cudaMemcpy(hm.data(), E->dmem, hm.size() * sizeof(EnsMember), cudaMemcpyDeviceToHost));
+      double tmax = 0.0;
+      for (const auto& g : E->groups)
+        tmax = std::max(tmax, 1e-6 * (double)(hm[g.back()].t1 - hm[g.front()].t0));
+      if (best_t < 0.0 || tmax < best_t) {
+        best_t = tmax;
+        best_shape = sh;
+        best_nblocks = E->nblocks;
+        best_groups = E->groups;
+        best_gnb = E->gnb;
+      }
+      for (int m = 0; m < nm; ++m) {
+        last2[m] = last1[m];
+        last1[m] = {E->nb[m], ms[m]};
+        double sm = 0.0, pm = ms[m] * E->nb[m];  // one measurement: all parallel
+        const int b1 = last1[m].first, b2 = last2[m].first;
+        if (b2 > 0 && b2 != b1) {
+          const double t1 = last1[m].second, t2 = last2[m].second;
+          const double x1 = 1.0 / b1, x2 = 1.0 / b2;
+          const double pf = (t1 - t2) / (x1 - x2);
+          const double sf = t1 - pf * x1;
+          if (pf > 0.0 && sf >= 0.0) {
+            sm = sf;
+            pm = pf;
+          }
+        }
+        sv[m] = sm;
+        pv[m] = pm;
+        fs[m] = sm;
+        fpt[m] = pm * threads;
+      }
+      have_fit = true;
+      for (int m = 0; m < nm; ++m)
+        CK(cudaMemcpyAsync(E->hmem[m].u, E->backup + E->state_off[m],
+                           (size_t)4 * E->grids[m]->T.ng * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      CK(cudaMemcpyAsync(E->dslots, E->dslots_backup, (size_t)2 * nm * sizeof(int), cudaMemcpyDeviceToDevice, st));
+      CK(cudaStreamSynchronize(st));
+      ens_plan(sv, pv, NB, E->groups, E->gnb);
+    }
   }
-  if (rounds > 0) {  // keep the best split measured (the last proposal was not run)
-    E->nb = best_nb;
-    if (int rc = ens_upload_split(E)) return rc;
-  }
+  // keep the best measured launch (shape, groups, split)
+  E->shape = best_shape;
+  E->groups = best_groups;
+  E->gnb = best_gnb;
+  int NB = 0, threads = 0;
+  if (ens_max_blocks(best_shape, &NB, &threads, nullptr) != 0) return fail(SWE_ERR_CUDA, "ensemble: occupancy query failed");
+  E->nblocks = NB;
+  (void)best_nblocks;
+  return ens_upload_split(E);
+}
+
+extern "C" int swe_ensemble_shape(const swe_ensemble* E, int* threads, int* blocks_per_sm, int* nblocks,
+                                  int* ngroups, int* member_group) {
+  if (!E) return fail(SWE_ERR_INVALID_ARG, "ensemble is NULL");
+  int NB = 0, t = 0, per = 0;
+  if (ens_max_blocks(E->shape, &NB, &t, &per) != 0) return fail(SWE_ERR_CUDA, "ensemble: occupancy query failed");
+  if (threads) *threads = t;
+  if (blocks_per_sm) *blocks_per_sm = per;
+  if (nblocks) *nblocks = E->nblocks;
+  if (ngroups) *ngroups = (int)E->groups.size();
+  if (member_group)
+    for (size_t g = 0; g < E->groups.size(); ++g)
+      for (int m : E->groups[g]) member_group[m] = (int)g;
+  return SWE_OK;
+}
+
+extern "C" int swe_ensemble_work(swe_ensemble* E, double* flop, void* stream) {
+  if (!E || !flop) return fail(SWE_ERR_INVALID_ARG, "ensemble and flop are required");
+  CK(cudaStreamSynchronize(S(stream)));
+  std::vector<DevStats> ds(E->nmem);
+  CK(cudaMemcpy(ds.data(), E->dstats, ds.size() * sizeof(DevStats), cudaMemcpyDeviceToHost));
+  double f = 0.0;
+  for (int m = 0; m < E->nmem; ++m)
+    f += (double)E->grids[m]->T.ng *
+         (kFlopIter * (double)ds[m].n_iter + kFlopWjv * (double)ds[m].n_wjv + kFlopComb * (double)ds[m].comb_terms);
+  *flop = f;
   return SWE_OK;
 }
 

@@ -81,6 +81,16 @@ def test_full_ensemble_matches_single_trajectories_tuned_and_graphed():
     st = E.stats()
     assert all(x == 0 for x in st["status"])
     assert sum(st["blocks"]) > 0 and min(st["blocks"]) >= 1
+    # the tuned launch is one of the shapes; every member is in exactly one
+    # group, a group's members share its block count, the groups fit the launch
+    sh = E.shape()
+    assert (sh["threads"], sh["blocks_per_sm"]) in {(96, 4), (128, 3), (192, 2), (384, 1)}
+    mg = sh["member_group"]
+    assert sorted(set(mg)) == list(range(sh["groups"]))
+    nbg = {}
+    for m, g in enumerate(mg):
+        assert nbg.setdefault(g, st["blocks"][m]) == st["blocks"][m]
+    assert sum(nbg.values()) == sh["nblocks"] <= 152 * sh["blocks_per_sm"]
     # eager run (fresh trajectories: no Krylov size carried from the tuning runs)
     E.reset()
     E.run()
