@@ -32,3 +32,26 @@ def trajectory(scheme: str, level: int, seed: int, amp: float, dt: float, nsteps
             u_prev = u
         u = u_next
     return u, decisions, njv
+
+
+def diagnostics_run(scheme: str, level: int, seed: int, amp: float, dt: float, nsteps: int, tol: float,
+                    gamma_h: float):
+    """The oracle trajectory of ``scheme`` with the conservation diagnostics
+    (total mass, energy, potential enstrophy) of the state after every step."""
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    from oracle.phipm import PhiOpts
+    from oracle.schemes import KrylovPhi, step
+    from oracle.swe import make_swe
+    from paper_1805_02144_gb300.inputs import balanced_state
+    s = make_swe(level, gamma_h=gamma_h)
+    u = balanced_state(s.grid.x, seed, amp)
+    kp = KrylovPhi(s, PhiOpts(tol=tol))
+    diag = [(s.mass(u), s.energy(u), s.potential_enstrophy(u))]
+    u_prev = None
+    for _ in range(nsteps):
+        u_next = step(scheme, s, u, dt, kp, u_prev=u_prev)
+        if scheme == "epi3":
+            u_prev = u
+        u = u_next
+        diag.append((s.mass(u), s.energy(u), s.potential_enstrophy(u)))
+    return u, diag
