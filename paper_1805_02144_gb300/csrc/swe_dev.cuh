@@ -69,10 +69,18 @@ __device__ __forceinline__ float ldtab(const float* p) {
       : "=f"(v) : "l"(p), "l"(l2_evict_first_policy()));
   return v;
 }
+__device__ __forceinline__ unsigned long long l2_evict_last_policy() {
+  unsigned long long pol;
+  asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+// Neighbour indices start every stencil's dependent chain (index -> gather)
+// and are read by both passes of every J x: they are kept in L2 (evict-last)
+// so that the chain starts with an L2 hit; the coefficient tables stream.
 __device__ __forceinline__ int ldtabi(const int32_t* p) {
   int v;
   asm("ld.global.nc.L1::no_allocate.L2::cache_hint.s32 %0, [%1], %2;"
-      : "=r"(v) : "l"(p), "l"(l2_evict_first_policy()));
+      : "=r"(v) : "l"(p), "l"(l2_evict_last_policy()));
   return v;
 }
 
