@@ -651,10 +651,14 @@ def gpu_arm(args) -> None:
     t_ms = max_over_ranks(sum(ms), dist, "cuda")
     value = job_rate(world, args.steps, t_ms)
 
-    # end to end through the public API: pinned host state in, host state out
+    # end to end through the public API: pinned host state in, host state out,
+    # over the same steps as the timed loop (the same warm-up from u0 with a
+    # fresh scheme state, so every step does the same work)
     n = G.n
+    st = SchemeState(G)
+    _, uw_e2e, _ = timed_steps(G, u0, SCHEME, DT, args.warmup, opts, flush, state=st)
     h_in = torch.empty(n, dtype=torch.float64, pin_memory=True)
-    h_in.copy_(ucur.cpu())
+    h_in.copy_(uw_e2e.cpu())
     h_out = torch.empty(n, dtype=torch.float64, pin_memory=True)
     d_in, d_out = torch.empty_like(u0), torch.empty_like(u0)
     ev2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
