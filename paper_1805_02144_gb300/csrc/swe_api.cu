@@ -1981,7 +1981,7 @@ extern "C" int swe_ensemble_tune(swe_ensemble* E, int rounds, void* stream) {
                        cudaMemcpyDeviceToDevice, st));
   CK(cudaMemcpyAsync(E->dslots_backup, E->dslots, (size_t)2 * E->nmem * sizeof(int), cudaMemcpyDeviceToDevice, st));
   const int nm = E->nmem;
-  int best_shape = E->shape, best_nblocks = E->nblocks;
+  int best_shape = E->shape;
   std::vector<std::vector<int>> best_groups = E->groups;
   std::vector<int> best_gnb = E->gnb;
   double best_t = -1.0;
@@ -2028,7 +2028,6 @@ extern "C" int swe_ensemble_tune(swe_ensemble* E, int rounds, void* stream) {
       if (best_t < 0.0 || tmax < best_t) {
         best_t = tmax;
         best_shape = sh;
-        best_nblocks = E->nblocks;
         best_groups = E->groups;
         best_gnb = E->gnb;
       }
@@ -2068,7 +2067,6 @@ extern "C" int swe_ensemble_tune(swe_ensemble* E, int rounds, void* stream) {
   int NB = 0, threads = 0;
   if (ens_max_blocks(best_shape, &NB, &threads, nullptr) != 0) return fail(SWE_ERR_CUDA, "ensemble: occupancy query failed");
   E->nblocks = NB;
-  (void)best_nblocks;
   return ens_upload_split(E);
 }
 
