@@ -229,3 +229,28 @@ def test_chosen_update_is_applied_to_the_next_attempt():
     for k in range(len(st.trace) - 1):
         m_new, m, take_tau = calls[k]
         assert st.trace[k + 1].m == (m if take_tau else m_new), k
+
+
+@pytest.mark.parametrize("pattern", [(0, 1), (1, 1, 0, 1), (0, 0, 0, 1, 1)])
+def test_relative_tolerance_makes_the_decisions_scale_invariant(pattern):
+    """Reading R7: with s = max_l ||v_l|| the accept test is invariant under
+    v_l -> c v_l, so the same decisions are taken and y scales by c; with the
+    absolute test (s = 1) a large c forces more work."""
+    from conftest import oracle_swe
+    from paper_1805_02144_gb300.inputs import balanced_state, random_vector
+    s = oracle_swe(2)
+    u = balanced_state(s.grid.x, 1, 400.0)
+    dt = 7200.0
+    v = [None if not on else random_vector(s.n, 30 + i) for i, on in enumerate(pattern)]
+    run = lambda vv, mode: phipm.phipm_simul_iom2(lambda x: dt * s.Jv(u, x), [0.5, 1.0], vv,
+                                                  PhiOpts(tol=1e-8, tol_mode=mode), s.nA)
+    W1, st1 = run(v, "relative")
+    c = 1e6
+    Wc, stc = run([None if x is None else c * x for x in v], "relative")
+    assert [(a.m, a.accepted) for a in st1.trace] == [(a.m, a.accepted) for a in stc.trace]
+    for a, b in zip(W1, Wc):
+        assert np.linalg.norm(b - c * a) <= 1e-12 * np.linalg.norm(c * a)
+    # the absolute test sees the scaled error estimate against the same Tol
+    _, sta = run([None if x is None else c * x for x in v], "absolute")
+    _, st0 = run(v, "absolute")
+    assert sta.n_jv > st0.n_jv
