@@ -124,40 +124,43 @@ __device__ void taylor_phi(Shared& sh, int m, int p, double tau, double hnorm, c
   double acc = (r == M - 1) ? 1.0 : 0.0;
   if (r < M) sh.x[r] = acc;
   __syncthreads();
-  // terms alternate between sh.x and sh.y: one block barrier per term
-  double* buf[2] = {sh.x, sh.y};
-  int c = 0;
-  for (int step = 0; step < s; ++step) {
-    // buf[c] holds the current term (starting with the vector itself)
-    for (int k = 1; k <= TAYLOR_TERMS; ++k) {
-      const double* xc = buf[c];
-      double v = 0.0;
-      if (r < m) {
-        v = cd * xc[r];
-        if (r > 0) v = fma(cl, xc[r - 1], v);
-        if (r < m - 1) v = fma(cu, xc[r + 1], v);
-        if (iom > 2) v = hup_row(hup, iom, r, m, tau, xc, v);
-        if (r == 0) v += xc[m];
-        v *= sh.ck[k];
-      } else if (r < m + p) {
-        v = xc[r + 1] * sh.ck[k];
+  // terms alternate between sh.x and sh.y: one barrier per term among the
+  // warps that hold rows (named barrier 1, nact threads); the other warps of
+  // the block wait at the block barrier below
+  const int nact = ((M + 31) / 32) * 32;
+  if (r < nact) {
+    double* buf[2] = {sh.x, sh.y};
+    int c = 0;
+    for (int step = 0; step < s; ++step) {
+      // buf[c] holds the current term (starting with the vector itself)
+      for (int k = 1; k <= TAYLOR_TERMS; ++k) {
+        const double* xc = buf[c];
+        double v = 0.0;
+        if (r < m) {
+          v = cd * xc[r];
+          if (r > 0) v = fma(cl, xc[r - 1], v);
+          if (r < m - 1) v = fma(cu, xc[r + 1], v);
+          if (iom > 2) v = hup_row(hup, iom, r, m, tau, xc, v);
+          if (r == 0) v += xc[m];
+          v *= sh.ck[k];
+        } else if (r < m + p) {
+          v = xc[r + 1] * sh.ck[k];
+        }
+        if (r < M) {
+          buf[c ^ 1][r] = v;
+          acc += v;
+        }
+        asm volatile("bar.sync 1, %0;" ::"r"(nact) : "memory");
+        c ^= 1;
       }
-      if (r < M) {
-        buf[c ^ 1][r] = v;
-        acc += v;
-      }
-      __syncthreads();
+      // the buffer read by the last term is free again: the step's sum goes there
+      if (r < M) buf[c ^ 1][r] = acc;
+      asm volatile("bar.sync 1, %0;" ::"r"(nact) : "memory");
       c ^= 1;
     }
-    // the buffer read by the last term is free again: the step's sum goes there
-    if (r < M) buf[c ^ 1][r] = acc;
-    __syncthreads();
-    c ^= 1;
+    if (c != 0 && r < M) sh.x[r] = acc;  // leave x in sh.x
   }
-  if (c != 0) {  // leave x in sh.x
-    if (r < M) sh.x[r] = acc;
-    __syncthreads();
-  }
+  __syncthreads();
   // phi_p(tau H) e_1 = tau H phi_{p+1}(tau H) e_1 + e_1 / p!   (Eq. eq3.7)
   if (r < m) {
     double v = cd * sh.x[r];
