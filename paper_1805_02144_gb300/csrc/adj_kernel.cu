@@ -210,9 +210,9 @@ __device__ __forceinline__ void adj_abort(const AdjArgs& a, SH& sh, int code) {
 
 // Wide grid reduction: nv dot products <vecs_r, Y> over all cells (vecs_r for
 // r < nv0: raw basis slots of substep k; r = nv0, nv0+1: <r_m, r_{m-2}>,
-// <r_m, r_{m-1}>), summed per block in a fixed order, then over blocks in
-// block order by block 0, which runs `last()` with all its threads between
-// two grid barriers.
+// <r_m, r_{m-1}>), summed per block in a fixed order, then over blocks in a
+// fixed order (sum_strided) by block 0, which runs `last()` with all its
+// threads between two grid barriers.
 template <class LastFn>
 __device__ bool adj_wide_reduce(const AdjArgs& a, AdjShared& sh, const CellLoop& CL, int k, const TapeSub& S,
                                 int m, LastFn last) {
@@ -241,14 +241,12 @@ __device__ bool adj_wide_reduce(const AdjArgs& a, AdjShared& sh, const CellLoop&
     block_sum<1>(v1, sh.red);
     if (threadIdx.x == 0) a.partw[(size_t)sh.gb * ADJ_KW + r] = v1[0];
   }
-  // all block totals published; block 0 sums them in block order and runs
+  // all block totals published; block 0 sums them in a fixed order and runs
   // `last` with all its threads while the others wait at the second barrier
   if (!grid_barrier(a, sh, AP_A)) return false;
   if (sh.gb == 0) {
     for (int r = threadIdx.x; r < nv; r += blockDim.x) {
-      double s = 0.0;
-      for (int b = 0; b < sh.gn; ++b) s += __ldcg(a.partw + (size_t)b * ADJ_KW + r);
-      a.ctrl->wide[r] = s;
+      a.ctrl->wide[r] = sum_strided(a.partw + r, ADJ_KW, sh.gn);
     }
     __syncthreads();
     last();

@@ -35,8 +35,42 @@ struct CellLoop {
 #define FOR_CELLS(i) for (int i = CL.first; i < CL.end; i += CL.step)
 
 // ---------------------------------------------------------------------------
-// block reductions in a fixed order
+// Reductions in a fixed order.  An FP64 add has a dependent latency of about
+// 64 cycles on this part (a shuffle plus add about 100), so the sums over
+// blocks below load their operands together and add them as trees of fixed
+// shape; the shape depends only on the launch (threads per block, blocks), so
+// results are reproducible.
 // ---------------------------------------------------------------------------
+
+// In-place pairwise tree over q[0..S) (S a power of two): q[0] = the total.
+template <int S, int K>
+__device__ __forceinline__ void pair_tree(double (&q)[S][K]) {
+#pragma unroll
+  for (int w = S / 2; w >= 1; w >>= 1)
+#pragma unroll
+    for (int s = 0; s < w; ++s)
+#pragma unroll
+      for (int k = 0; k < K; ++k) q[s][k] = q[2 * s][k] + q[2 * s + 1][k];
+}
+
+// Sum of p[b * stride] over b in [0, n): chunks of eight consecutive b, each
+// loaded together and added as a pairwise tree, chunk totals added in order.
+__device__ __forceinline__ double sum_strided(const double* p, size_t stride, int n) {
+  double t = 0.0;
+  for (int b0 = 0; b0 < n; b0 += 8) {
+    double q[8][1];
+#pragma unroll
+    for (int s = 0; s < 8; ++s) q[s][0] = b0 + s < n ? __ldcg(p + (size_t)(b0 + s) * stride) : 0.0;
+    pair_tree(q);
+    t += q[0][0];
+  }
+  return t;
+}
+
+// Block totals of K per-thread values: a shuffle tree in every warp, then
+// thread 0 adds the warp totals in warp order (a short serial chain: a tree
+// here costs registers that the 64-register FP32 variants spill).  Thread 0
+// holds the totals on return.
 template <int K>
 __device__ __forceinline__ void block_sum(double (&v)[K], double* sred) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -56,6 +90,34 @@ __device__ __forceinline__ void block_sum(double (&v)[K], double* sred) {
     }
   }
   __syncthreads();
+}
+
+// Totals over gn blocks of K values (value k of block b at part[k * gn + b]),
+// by one warp: lane l takes blocks l, l + 32, ... in chunks whose loads are
+// issued together and added as a pairwise tree, then a shuffle tree.  Lane 0
+// holds the totals on return.
+template <int K>
+__device__ __forceinline__ void warp_sum_blocks(const double* part, int gn, double (&t)[K]) {
+  constexpr int S = K <= 2 ? 8 : (K <= 4 ? 4 : 1);
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 0; k < K; ++k) t[k] = 0.0;
+  for (int b0 = lane; b0 < gn; b0 += 32 * S) {
+    double q[S][K];
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      const int b = b0 + 32 * s;
+#pragma unroll
+      for (int k = 0; k < K; ++k) q[s][k] = b < gn ? __ldcg(part + (size_t)k * gn + b) : 0.0;
+    }
+    pair_tree(q);
+#pragma unroll
+    for (int k = 0; k < K; ++k) t[k] += q[0][k];
+  }
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t[k] += __shfl_down_sync(0xffffffffu, t[k], o);
 }
 
 template <class A, class SH>
@@ -81,13 +143,12 @@ __device__ bool grid_barrier(const A& a, SH& sh, int phase) {
 }
 
 // Grid reduction of K per-thread partials, then a barrier.  Each block sums
-// its threads in a fixed order and publishes its totals (value k of block b
-// at part[k * gn + b]); warp 0 of the block that arrives last sums them over
-// blocks (lane l takes blocks l, l+32, ..., then a fixed shuffle tree, so the
-// result is bitwise reproducible), stores them in ctrl->red[], runs
-// post(ctrl, true, sums) on its lane 0 (the sums passed in registers, so the
-// post reads nothing back over the bus) and publishes; the other blocks wait
-// for the publication.
+// its threads (block_sum) and publishes its totals (value k of block b at
+// part[k * gn + b]); warp 0 of the block that arrives last sums them over
+// blocks (warp_sum_blocks: a fixed order, so the result is reproducible),
+// stores them in ctrl->red[], runs post(ctrl, true, sums) on its lane 0 (the
+// sums passed in registers, so the post reads nothing back over the bus) and
+// publishes; the other blocks wait for the publication.
 // The K sums of a grid reduction, handed to the post function by value.
 template <int K>
 struct RedSums {
@@ -115,19 +176,7 @@ __device__ bool grid_reduce(const A& a, SH& sh, double (&v)[K], int phase, Post 
     if (lastu) {
       __threadfence();
       double t[K];
-#pragma unroll
-      for (int k = 0; k < K; ++k) t[k] = 0.0;
-      // unrolled so that a lane's loads are in flight together, about eight
-      // values at a time (the sum order over b is unchanged)
-      constexpr int kUnroll = K >= 8 ? 1 : (K >= 4 ? 2 : 8 / K);
-#pragma unroll kUnroll
-      for (int b = threadIdx.x; b < gn; b += 32)
-#pragma unroll
-        for (int k = 0; k < K; ++k) t[k] += __ldcg(a.part + (size_t)k * gn + b);
-#pragma unroll
-      for (int k = 0; k < K; ++k)
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) t[k] += __shfl_down_sync(0xffffffffu, t[k], o);
+      warp_sum_blocks<K>(a.part, gn, t);
       if (threadIdx.x == 0) {
         auto* vc = make_volatile(a.ctrl);
         RedSums<K> r;
@@ -155,7 +204,7 @@ __device__ bool grid_reduce(const A& a, SH& sh, double (&v)[K], int phase, Post 
 
 // Grid reduction of nv <= blockDim.x values whose block totals thread 0 of
 // every block has stored at partw[gb * WIDE_STRIDE + r].  Threads r < nv of
-// the block that arrives last each sum value r over blocks in block order
+// the block that arrives last each sum value r over blocks (sum_strided)
 // into ctrl->wide[r]; its thread 0 runs post(ctrl) and publishes; the other
 // blocks wait for the publication.
 template <class A, class SH, class Post>
@@ -173,8 +222,7 @@ __device__ bool grid_reduce_wide(const A& a, SH& sh, int nv, int phase, Post pos
   __syncthreads();
   if (w_last) {
     if ((int)threadIdx.x < nv) {
-      double t = 0.0;
-      for (int b = 0; b < sh.gn; ++b) t += __ldcg(a.partw + (size_t)b * WIDE_STRIDE + threadIdx.x);
+      const double t = sum_strided(a.partw + threadIdx.x, WIDE_STRIDE, sh.gn);
       ((volatile double*)a.ctrl->wide)[threadIdx.x] = t;
     }
     __syncthreads();

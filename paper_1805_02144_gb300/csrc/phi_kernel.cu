@@ -6,11 +6,11 @@
 //
 // Work split: block b owns a contiguous range of cells (space-filling-curve
 // order, so its stencil gathers stay mostly inside the range).  Phases are
-// separated by bounded grid barriers; reductions are summed per block in a
-// fixed order, then over blocks in block order by the last block to arrive,
-// so results are bitwise reproducible for a given grid size.  The small
-// decisions (exponential of the (m+p+1)-square augmented matrix, controller)
-// run on one warp of block 0 while the other blocks wait at the barrier.
+// separated by bounded grid barriers; reductions are summed per block as a
+// fixed tree, then over blocks as a fixed tree by the last block to arrive,
+// so results are bitwise reproducible for a given grid and launch shape.
+// The small decisions (exponential of the (m+p+1)-square augmented matrix,
+// controller) run on block 0 while the other blocks wait at the barrier.
 //
 // The Krylov basis is stored unnormalised: raw slot j holds z_j (slot 0 is
 // w_p itself) and v_j = sig[j] * raw_j with sig[0] = 1/beta,
@@ -477,6 +477,37 @@ __device__ __forceinline__ double h_entry(volatile PhiCtrl* c, int i, int j) {
   return c->hup[i * KMAX + j];
 }
 
+// Completes IOM2 column j of Algorithm 1 step 2(i) from ss = |r_{j+1}|^2, the
+// squared norm of the raw vector the orthogonalisation of column j wrote:
+// h_{j+1,j} = |r_{j+1}| and sig[j+1] = 1 / h_{j+1,j}, or a happy breakdown
+// (invariant subspace) when h_{j+1,j} is at the rounding floor of the
+// column's window coefficients.  Runs on the lane that publishes a grid
+// reduction; returns false on a breakdown or a non-finite norm.
+__device__ __forceinline__ bool complete_column(volatile PhiCtrl* c, GridSync* gs, int j, double ss,
+                                                double bd, bool leader) {
+  const double hn = sqrt(ss);
+  const double ref = fabs(c->hd[j]) + (j > 0 ? fabs(c->hu[j - 1]) : 0.0);
+  c->size = j + 1;
+  if (leader) {
+    c->n_jv += 1;
+    c->n_iter += 1;
+  }
+  if (!isfinite(hn) || !isfinite(ref)) {
+    c->status = SWE_ERR_NONFINITE;
+    atomicCAS(&gs->abort, 0, SWE_ERR_NONFINITE);
+    return false;
+  }
+  if (hn <= bd * ref) {
+    c->broken = 1;
+    c->hl[j + 1] = 0.0;
+    c->sig[j + 1] = 0.0;
+    return false;
+  }
+  c->hl[j + 1] = hn;
+  c->sig[j + 1] = 1.0 / hn;
+  return true;
+}
+
 // Algorithm 1 for one call, executed by the sh.gn blocks of a group.  Returns
 // false when the launch is being aborted (every block of the group returns
 // at the same barrier or at the next one).
@@ -650,10 +681,13 @@ __device__ bool phi_run(const PhiArgsT<R>& a, Shared& sh) {
           }
           m_req = min(m_req, KMAX);
           // ---- IOM2: extend the basis to m_req columns (step 2(i)) --------
-          // Per column j: pass 2 (z = A v_j and the two window dots) and the
-          // fused orthogonalisation + pass 1 of the next vector, each ended
-          // by one grid reduction.  Pass-1 planes of raw slot j: Laplacian in
-          // Lring[j % 3], scalar/vector planes in SQ.
+          // Per column j: pass 2 (A r_j and the two window dots) and the
+          // fused orthogonalisation + pass 1 of the next vector.  Pass 2 is
+          // linear, so it runs on the raw vector before its norm is known:
+          // the norm's partial sums ride in the next column's reduction, and
+          // the orthogonalisation ends in a plain barrier (the last column's
+          // norm is reduced on its own).  Pass-1 planes of raw slot j:
+          // Laplacian in Lring[j % 3], scalar/vector planes in SQ.
           R* SQ = a.tmp + (size_t)4 * ng;
           // windows wider than two (iom > 2, up to full orthogonalisation):
           // the same three phases with w window dots in one wide reduction
@@ -739,74 +773,70 @@ __device__ bool phi_run(const PhiArgsT<R>& a, Shared& sh) {
             };
             if (!grid_reduce<1>(a, sh, wn, PH_ORTH, post_wnorm)) return false;
           }
-          while (vldi(&C->size) < m_req && !vldi(&C->broken)) {
-            const int j = vldi(&C->size);
-            R* rj = B.raw(j, n, p);
-            R* rj1 = B.raw(j + 1, n, p);
-            R* rjm = j > 0 ? B.raw(j - 1, n, p) : nullptr;
-            R* Lj = a.Lring + (size_t)(j % 3) * n;
-            R* Ljm = a.Lring + (size_t)((j + 2) % 3) * n;
-            R* Lj1 = a.Lring + (size_t)((j + 1) % 3) * n;
-            const double sj = vld(&C->sig[j]);
-            const double sjm = j > 0 ? vld(&C->sig[j - 1]) : 0.0;
-            if (j == 0) {
-              FOR_CELLS(i)
-                pass1_cell<MODE_J, R, IL>(T, i, rj, R(1), a.u_lin, Lj, SQ);
-              if (!grid_barrier(a, sh, PH_K_PASS1)) return false;
-            }
-            const R zs = (R)(a.dt * sj);
-            R d0 = R(0), d1 = R(0);
-            FOR_CELLS(i) {
-              R o[4];
-              pass2_cell<MODE_J, R, IL>(T, i, rj, R(1), Lj, SQ, a.aux, o);
-#pragma unroll
-              for (int c = 0; c < 4; ++c) {
-                const size_t e = (size_t)c * ng + i;
-                R z = zs * o[c];
-                a.Zbuf[e] = z;
-                if (rjm) d0 = fma(z, rjm[e], d0);
-                d1 = fma(z, rj[e], d1);
-              }
-            }
-            double v[2] = {(double)d0, (double)d1};
-            auto post_dots = [j, sj, sjm](volatile PhiCtrl* c, bool, const auto& r) {
-              if (j > 0) c->hu[j - 1] = sjm * r[0];
-              c->hd[j] = sj * r[1];
-            };
-            if (!grid_reduce<2>(a, sh, v, PH_K_PASS2, post_dots)) return false;
-            // z' = z - h_{j-1,j} v_{j-1} - h_{j,j} v_j with its pass-1 planes
-            const double hdj = vld(&C->hd[j]);
-            const double huj = j > 0 ? vld(&C->hu[j - 1]) : 0.0;
-            const R am = j > 0 ? (R)(huj * sjm) : R(0);
-            const R aj = (R)(hdj * sj);
-            R nrm = R(0);
-            FOR_CELLS(i)
-              nrm += orth_pass1_cell<R, IL>(T, i, a.Zbuf, rj, rjm, aj, am, Lj, Ljm, rj1, Lj1, a.u_lin, SQ);
-            double w[1] = {(double)nrm};
+          if (vldi(&C->size) < m_req && !vldi(&C->broken)) {
+            int j = vldi(&C->size);
+            R nrm = R(0);      // this thread's share of |r_j|^2 while column j-1 is open
+            bool pend = false;  // column j-1 open: its norm joins column j's reduction
             GridSync* gs = a.sync;
-            auto post_norm = [gs, j, bd, hdj, huj](volatile PhiCtrl* c, bool leader, const auto& r) {
-              double hn = sqrt(r[0]);
-              double ref = fabs(hdj) + (j > 0 ? fabs(huj) : 0.0);
-              c->size = j + 1;
-              if (leader) {
-                c->n_jv += 1;
-                c->n_iter += 1;
+            const double dt = a.dt;
+            while (true) {
+              R* rj = B.raw(j, n, p);
+              R* rj1 = B.raw(j + 1, n, p);
+              R* rjm = j > 0 ? B.raw(j - 1, n, p) : nullptr;
+              R* Lj = a.Lring + (size_t)(j % 3) * n;
+              R* Ljm = a.Lring + (size_t)((j + 2) % 3) * n;
+              R* Lj1 = a.Lring + (size_t)((j + 1) % 3) * n;
+              if (j == 0) {
+                FOR_CELLS(i)
+                  pass1_cell<MODE_J, R, IL>(T, i, rj, R(1), a.u_lin, Lj, SQ);
+                if (!grid_barrier(a, sh, PH_K_PASS1)) return false;
               }
-              if (!isfinite(hn) || !isfinite(ref)) {
-                c->status = SWE_ERR_NONFINITE;
-                atomicCAS(&gs->abort, 0, SWE_ERR_NONFINITE);
-                return;
+              // pass 2: A r_j of the raw vector (its scale may not be known yet)
+              R d0 = R(0), d1 = R(0);
+              FOR_CELLS(i) {
+                R o[4];
+                pass2_cell<MODE_J, R, IL>(T, i, rj, R(1), Lj, SQ, a.aux, o);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                  const size_t e = (size_t)c * ng + i;
+                  a.Zbuf[e] = o[c];
+                  if (rjm) d0 = fma(o[c], rjm[e], d0);
+                  d1 = fma(o[c], rj[e], d1);
+                }
               }
-              if (hn <= bd * ref) {  // happy breakdown: invariant subspace
-                c->broken = 1;
-                c->hl[j + 1] = 0.0;
-                c->sig[j + 1] = 0.0;
-              } else {
-                c->hl[j + 1] = hn;
-                c->sig[j + 1] = 1.0 / hn;
+              // one reduction: |r_j|^2 (closing column j-1), <A r_j, r_{j-1}>, <A r_j, r_j>
+              double v[3] = {(double)nrm, (double)d0, (double)d1};
+              auto post_col = [gs, j, pend, bd, dt](volatile PhiCtrl* c, bool leader, const auto& r) {
+                if (pend && !complete_column(c, gs, j - 1, r[0], bd, leader)) return;
+                const double sj = c->sig[j];
+                const double zs = dt * sj;  // z = zs A r_j = dt A v_j
+                if (j > 0) c->hu[j - 1] = c->sig[j - 1] * (zs * r[1]);
+                c->hd[j] = sj * (zs * r[2]);
+              };
+              if (!grid_reduce<3>(a, sh, v, PH_K_PASS2, post_col)) return false;
+              if (vldi(&C->broken)) break;  // column j-1 ended the basis; A r_j unused
+              // z' = z - h_{j-1,j} v_{j-1} - h_{j,j} v_j with its pass-1 planes
+              const double sj = vld(&C->sig[j]);
+              const double sjm = j > 0 ? vld(&C->sig[j - 1]) : 0.0;
+              const R zs = (R)(dt * sj);
+              const R am = j > 0 ? (R)(vld(&C->hu[j - 1]) * sjm) : R(0);
+              const R aj = (R)(vld(&C->hd[j]) * sj);
+              nrm = R(0);
+              FOR_CELLS(i)
+                nrm += orth_pass1_cell<R, IL>(T, i, a.Zbuf, zs, rj, rjm, aj, am, Lj, Ljm, rj1, Lj1, a.u_lin, SQ);
+              if (j + 1 < m_req) {  // pass 2 of r_{j+1} needs its planes on every cell
+                if (!grid_barrier(a, sh, PH_ORTH)) return false;
+                pend = true;
+                ++j;
+                continue;
               }
-            };
-            if (!grid_reduce<1>(a, sh, w, PH_ORTH, post_norm)) return false;
+              double w[1] = {(double)nrm};
+              auto post_last = [gs, j, bd](volatile PhiCtrl* c, bool leader, const auto& r) {
+                complete_column(c, gs, j, r[0], bd, leader);
+              };
+              if (!grid_reduce<1>(a, sh, w, PH_ORTH, post_last)) return false;
+              break;
+            }
           }
         }
         // ---- exponential, error estimate, controller (steps 2(ii)-6) -------

@@ -174,17 +174,18 @@ __device__ __forceinline__ void pass1_cell(const TablesT<R>& T, int i, const R* 
   st_planes<IL>(sq, ng, i, sv);
 }
 
-// Fused IOM2 orthogonalisation and pass 1 (MODE_J) at cell i.  z is A v_j
-// (complete on every cell), r_j and r_m the raw basis vectors j and j-1 with
-// their Laplacian planes Lj, Lm; aj, am the window coefficients with the
-// basis scales folded in (am = 0 and r_m, Lm unused for j = 0):
-//   z' = z - aj r_j - am r_m                          -> rnew (own cell)
-//   L z' = L z - aj L r_j - am L r_m                  -> Lnew (L is linear)
+// Fused IOM2 orthogonalisation and pass 1 (MODE_J) at cell i.  z is A r_j
+// of the raw basis vector r_j (complete on every cell) and zs the factor that
+// makes zs z the column's dt A v_j; r_j and r_m are the raw basis vectors j
+// and j-1 with their Laplacian planes Lj, Lm; aj, am the window coefficients
+// with the basis scales folded in (am = 0 and r_m, Lm unused for j = 0):
+//   z' = zs z - aj r_j - am r_m                       -> rnew (own cell)
+//   L z' = zs L z - aj L r_j - am L r_m               -> Lnew (L is linear)
 //   s', q' of z'                                      -> sq
 // and returns |z'|^2 of the cell.  No value of z' is gathered, so rnew may be
 // written while neighbours still read z.
 template <typename R, bool IL = false>
-__device__ __forceinline__ R orth_pass1_cell(const TablesT<R>& T, int i, const R* z, const R* rj,
+__device__ __forceinline__ R orth_pass1_cell(const TablesT<R>& T, int i, const R* z, R zs, const R* rj,
                                              const R* rm, R aj, R am, const R* Lj, const R* Lm,
                                              R* rnew, R* Lnew, const R* u, R* sq) {
   const int ng = T.ng;
@@ -197,8 +198,8 @@ __device__ __forceinline__ R orth_pass1_cell(const TablesT<R>& T, int i, const R
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
     const size_t e = (size_t)c * ng + i;
-    R v = fma(-aj, ld(rj + e), ld(z + e));
-    R lz = fma(-aj, Ljv[c], lap_cell(T, i, nb, z + (size_t)c * ng));
+    R v = fma(-aj, ld(rj + e), zs * ld(z + e));
+    R lz = fma(-aj, Ljv[c], zs * lap_cell(T, i, nb, z + (size_t)c * ng));
     if (rm) {
       v = fma(-am, ld(rm + e), v);
       lz = fma(-am, Lmv[c], lz);
