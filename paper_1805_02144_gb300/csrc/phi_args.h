@@ -71,6 +71,7 @@ struct PhiLaunch {
   const void* fn = nullptr;
   int threads = 0;
   int nblocks = 0;
+  int smem = 0;  // dynamic shared memory: the blocks' neighbour indices (0: read from global)
 };
 
 // Arguments of one persistent launch.  R is the precision of tables, vectors

@@ -511,7 +511,7 @@ __device__ __forceinline__ bool complete_column(volatile PhiCtrl* c, GridSync* g
 // Algorithm 1 for one call, executed by the sh.gn blocks of a group.  Returns
 // false when the launch is being aborted (every block of the group returns
 // at the same barrier or at the next one).
-template <typename R>
+template <typename R, bool STAGE = false>
 __device__ bool phi_run(const PhiArgsT<R>& a, Shared& sh) {
   const TablesT<R>& T = a.T;
   // happy-breakdown threshold relative to the window coefficients: near the
@@ -526,6 +526,26 @@ __device__ bool phi_run(const PhiArgsT<R>& a, Shared& sh) {
   const Range RG{min(ng, sh.gb * chunk), min(ng, (sh.gb + 1) * chunk)};
   const CellLoop CL(RG);
   PhiCtrl* C = a.ctrl;
+  // STAGE: the block's cells keep their neighbour indices in shared memory
+  // for the whole launch (dynamic shared memory of SLOTS x chunk indices,
+  // which the host grants; without it the indices stay in global memory).
+  // Without STAGE the view stays empty and the stencils compile to their
+  // global-memory loads alone.
+  NbrStage ST;
+  if constexpr (STAGE) {
+    extern __shared__ int32_t s_nbr[];
+    unsigned int dyn;
+    asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
+    if (chunk > 0 && (size_t)dyn >= (size_t)SLOTS * chunk * sizeof(int32_t)) {
+      for (int l = threadIdx.x; l < RG.c1 - RG.c0; l += blockDim.x)
+#pragma unroll
+        for (int k = 0; k < SLOTS; ++k) s_nbr[k * chunk + l] = __ldg(T.nbr + (size_t)k * ng + RG.c0 + l);
+      __syncthreads();
+      ST.s = s_nbr;
+      ST.c0 = RG.c0;
+      ST.stride = chunk;
+    }
+  }
 
   // ---- prologue: y = v_0, norms of the inputs -----------------------------
   if (threadIdx.x == 0) sh.t_last = globaltimer();
@@ -623,7 +643,7 @@ __device__ bool phi_run(const PhiArgsT<R>& a, Shared& sh) {
         R* wj = B.Wk + (size_t)j * n;
         if (nz_prev) {
           FOR_CELLS(i)
-            pass1_cell<MODE_J, R, IL>(T, i, wprev, R(1), a.u_lin, a.tmp, a.tmp + (size_t)4 * ng);
+            pass1_cell<MODE_J, R, IL>(T, i, wprev, R(1), a.u_lin, a.tmp, a.tmp + (size_t)4 * ng, ST);
           if (!grid_barrier(a, sh, PH_W_PASS1)) return false;
         }
         R clr[PMAX + 1];
@@ -633,7 +653,7 @@ __device__ bool phi_run(const PhiArgsT<R>& a, Shared& sh) {
         R sqs = R(0);
         FOR_CELLS(i) {
           R o[4] = {R(0), R(0), R(0), R(0)};
-          if (nz_prev) pass2_cell<MODE_J, R, IL>(T, i, wprev, R(1), a.tmp, a.tmp + (size_t)4 * ng, a.aux, o);
+          if (nz_prev) pass2_cell<MODE_J, R, IL>(T, i, wprev, R(1), a.tmp, a.tmp + (size_t)4 * ng, a.aux, o, ST);
 #pragma unroll
           for (int c = 0; c < 4; ++c) {
             const size_t e = (size_t)c * ng + i;
@@ -701,13 +721,13 @@ __device__ bool phi_run(const PhiArgsT<R>& a, Shared& sh) {
             const double sj = vld(&C->sig[j]);
             if (j == 0) {
               FOR_CELLS(i)
-                pass1_cell<MODE_J, R, IL>(T, i, rj, R(1), a.u_lin, Lj, SQ);
+                pass1_cell<MODE_J, R, IL>(T, i, rj, R(1), a.u_lin, Lj, SQ, ST);
               if (!grid_barrier(a, sh, PH_K_PASS1)) return false;
             }
             const R zs = (R)(a.dt * sj);
             FOR_CELLS(i) {
               R o[4];
-              pass2_cell<MODE_J, R, IL>(T, i, rj, R(1), Lj, SQ, a.aux, o);
+              pass2_cell<MODE_J, R, IL>(T, i, rj, R(1), Lj, SQ, a.aux, o, ST);
 #pragma unroll
               for (int c = 0; c < 4; ++c) a.Zbuf[(size_t)c * ng + i] = zs * o[c];
             }
@@ -788,14 +808,14 @@ __device__ bool phi_run(const PhiArgsT<R>& a, Shared& sh) {
               R* Lj1 = a.Lring + (size_t)((j + 1) % 3) * n;
               if (j == 0) {
                 FOR_CELLS(i)
-                  pass1_cell<MODE_J, R, IL>(T, i, rj, R(1), a.u_lin, Lj, SQ);
+                  pass1_cell<MODE_J, R, IL>(T, i, rj, R(1), a.u_lin, Lj, SQ, ST);
                 if (!grid_barrier(a, sh, PH_K_PASS1)) return false;
               }
               // pass 2: A r_j of the raw vector (its scale may not be known yet)
               R d0 = R(0), d1 = R(0);
               FOR_CELLS(i) {
                 R o[4];
-                pass2_cell<MODE_J, R, IL>(T, i, rj, R(1), Lj, SQ, a.aux, o);
+                pass2_cell<MODE_J, R, IL>(T, i, rj, R(1), Lj, SQ, a.aux, o, ST);
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
                   const size_t e = (size_t)c * ng + i;
@@ -823,7 +843,7 @@ __device__ bool phi_run(const PhiArgsT<R>& a, Shared& sh) {
               const R aj = (R)(vld(&C->hd[j]) * sj);
               nrm = R(0);
               FOR_CELLS(i)
-                nrm += orth_pass1_cell<R, IL>(T, i, a.Zbuf, zs, rj, rjm, aj, am, Lj, Ljm, rj1, Lj1, a.u_lin, SQ);
+                nrm += orth_pass1_cell<R, IL>(T, i, a.Zbuf, zs, rj, rjm, aj, am, Lj, Ljm, rj1, Lj1, a.u_lin, SQ, ST);
               if (j + 1 < m_req) {  // pass 2 of r_{j+1} needs its planes on every cell
                 if (!grid_barrier(a, sh, PH_ORTH)) return false;
                 pend = true;
@@ -1077,7 +1097,7 @@ int launch_ens_kernel(int shape, EnsMember* mem, const int* blk2mem, int nblocks
 // Instantiations (block size, minimum resident blocks per SM for the register
 // budget).  The body adapts to blockDim.x; the taylor exponential needs at
 // least m_max + p + 1 = 69 threads.
-template <typename R, int NT, int MINB>
+template <typename R, int NT, int MINB, bool STAGE = false>
 __global__ void __launch_bounds__(NT, MINB) phi_kernel(const __grid_constant__ PhiArgsT<R> a) {
   static_assert(NT % 32 == 0 && NT <= PHI_MAX_THREADS, "block size beyond the shared reduction scratch");
   __shared__ Shared sh;
@@ -1086,7 +1106,7 @@ __global__ void __launch_bounds__(NT, MINB) phi_kernel(const __grid_constant__ P
     sh.gn = gridDim.x;
   }
   __syncthreads();
-  phi_run<R>(a, sh);
+  phi_run<R, STAGE>(a, sh);
   phi_finish<R>(a, sh);
 }
 
@@ -1105,6 +1125,18 @@ static const PhiVariant kVariants[2][5] = {
      {(const void*)phi_kernel<float, 256, 2>, 256},
      {(const void*)phi_kernel<float, 128, 3>, 128},
      {(const void*)phi_kernel<float, 96, 4>, 96}},
+};
+
+// Instantiations whose blocks keep their neighbour indices in shared memory,
+// beside the plain ones they replace when the indices fit.  Only the FP32
+// stencils, bound by the latency of the index -> gather chain, have one; the
+// FP64 stencils are bound by the FP64 unit and run no faster staged.
+struct PhiStaged {
+  const void* plain;
+  const void* staged;
+};
+static const PhiStaged kStaged[] = {
+    {(const void*)phi_kernel<float, 512, 2>, (const void*)phi_kernel<float, 512, 2, true>},
 };
 
 // Picks the instantiation and block count for a grid of ng cells.  The FP64
@@ -1143,7 +1175,34 @@ int phi_select(int ng, int single, PhiLaunch* out) {
       out->nblocks = (int)nb;
     }
   }
-  return found ? 0 : -1;
+  if (!found) return -1;
+  // Each block's neighbour indices go to shared memory when the variant has a
+  // staged instantiation and they fit without lowering the occupancy the
+  // variant was ranked with.  The function's dynamic shared memory limit is
+  // raised to the device maximum (grids of other sizes share the function);
+  // the launch asks for what it needs.
+  out->smem = 0;
+  const void* staged = nullptr;
+  for (const PhiStaged& st : kStaged)
+    if (st.plain == out->fn) staged = st.staged;
+  if (!staged) return 0;
+  const long long chunk = (ng + out->nblocks - 1) / out->nblocks;
+  const long long need = (long long)SLOTS * chunk * (long long)sizeof(int32_t);
+  int optin = 0;
+  cudaFuncAttributes fa;
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess &&
+      cudaFuncGetAttributes(&fa, staged) == cudaSuccess && need + (long long)fa.sharedSizeBytes <= optin &&
+      cudaFuncSetAttribute(staged, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           optin - (int)fa.sharedSizeBytes) == cudaSuccess) {
+    int per = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, staged, out->threads, (size_t)need) == cudaSuccess &&
+        (long long)per * nsm >= out->nblocks) {
+      out->fn = staged;
+      out->smem = (int)need;
+    }
+  }
+  (void)cudaGetLastError();  // a refused attribute only leaves the indices in global memory
+  return 0;
 }
 
 // Cooperative launch (all blocks co-resident: the grid barriers need it).
@@ -1152,7 +1211,7 @@ int launch_phi_kernel(const PhiLaunch& L, const A& a, cudaStream_t stream) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(L.nblocks);
   cfg.blockDim = dim3(L.threads);
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = (size_t)L.smem;
   cfg.stream = stream;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;

@@ -93,10 +93,27 @@ __device__ __forceinline__ R lap_cell(const TablesT<R>& T, int i, const int (&nb
   return acc;
 }
 
+// Neighbour indices of a block's own cells [c0, c0 + stride) copied into
+// shared memory by a persistent launch: slot k of cell i at
+// s[k * stride + (i - c0)].  An empty view (s == nullptr) reads the table in
+// global memory.  Staged indices take the L2 round trip off the start of
+// every stencil's index -> gather chain.
+struct NbrStage {
+  const int32_t* s = nullptr;
+  int c0 = 0, stride = 0;
+};
+
 template <typename R>
-__device__ __forceinline__ void load_nbr(const TablesT<R>& T, int i, int (&nb)[SLOTS]) {
+__device__ __forceinline__ void load_nbr(const TablesT<R>& T, int i, int (&nb)[SLOTS],
+                                         const NbrStage& st = NbrStage()) {
+  if (st.s) {
+    const int32_t* q = st.s + (i - st.c0);
 #pragma unroll
-  for (int k = 0; k < SLOTS; ++k) nb[k] = ldtabi(T.nbr + (size_t)k * T.ng + i);
+    for (int k = 0; k < SLOTS; ++k) nb[k] = q[k * st.stride];
+  } else {
+#pragma unroll
+    for (int k = 0; k < SLOTS; ++k) nb[k] = ldtabi(T.nbr + (size_t)k * T.ng + i);
+  }
 }
 
 // The pass-1 planes (4 Laplacian, 4 scalar/vector) are planar, [4][ng], or
@@ -135,10 +152,10 @@ __device__ __forceinline__ void ld_planes(const R* base, int ng, int i, R (&v)[4
 //   MODE_Q: x = d.          -,       E = |d_u|^2/2,      q = d_u d_h
 template <int MODE, typename R, bool IL = false>
 __device__ __forceinline__ void pass1_cell(const TablesT<R>& T, int i, const R* x, R sx, const R* u,
-                                           R* Lout, R* sq) {
+                                           R* Lout, R* sq, const NbrStage& st = NbrStage()) {
   const int ng = T.ng;
   int nb[SLOTS];
-  load_nbr(T, i, nb);
+  load_nbr(T, i, nb, st);
   R xv[4];
 #pragma unroll
   for (int c = 0; c < 4; ++c) xv[c] = ld(x + (size_t)c * ng + i);
@@ -187,10 +204,11 @@ __device__ __forceinline__ void pass1_cell(const TablesT<R>& T, int i, const R* 
 template <typename R, bool IL = false>
 __device__ __forceinline__ R orth_pass1_cell(const TablesT<R>& T, int i, const R* z, R zs, const R* rj,
                                              const R* rm, R aj, R am, const R* Lj, const R* Lm,
-                                             R* rnew, R* Lnew, const R* u, R* sq) {
+                                             R* rnew, R* Lnew, const R* u, R* sq,
+                                             const NbrStage& st = NbrStage()) {
   const int ng = T.ng;
   int nb[SLOTS];
-  load_nbr(T, i, nb);
+  load_nbr(T, i, nb, st);
   R Ljv[4], Lmv[4] = {R(0), R(0), R(0), R(0)}, lzv[4];
   ld_planes<IL>(Lj, ng, i, Ljv);
   if (rm) ld_planes<IL>(Lm, ng, i, Lmv);
@@ -227,10 +245,11 @@ __device__ __forceinline__ R orth_pass1_cell(const TablesT<R>& T, int i, const R
 //   eta = V u + f, P = n x u.
 template <int MODE, typename R, bool IL = false>
 __device__ __forceinline__ void pass2_cell(const TablesT<R>& T, int i, const R* x, R sx, const R* Lp,
-                                           const R* sq, const R* aux, R out[4]) {
+                                           const R* sq, const R* aux, R out[4],
+                                           const NbrStage& st = NbrStage()) {
   const int ng = T.ng;
   int nb[SLOTS];
-  load_nbr(T, i, nb);
+  load_nbr(T, i, nb, st);
   // relative vorticity of x: V . x_u
   R vor = R(0);
 #pragma unroll
