@@ -6,7 +6,10 @@ target is the FP64 oracle within 1e-5 relative L2 in h and in the stacked
 velocity.  The 24-step level-8 run (12 h at dt = 1800 s) is compared with the
 FP64 GPU path, which the FP64 parity tests tie to the oracle within 1e-10;
 the oracle itself is compared directly on level 5 (24 steps) and level 8
-(2 steps).
+(2 steps).  Up to level 8 the FP32 kernel keeps each block's neighbour
+indices in shared memory; at level 9 they do not fit (207 KB per block at
+two blocks per SM) and the kernel that reads them from global memory runs,
+compared with the FP64 path over two steps.
 """
 import numpy as np
 import pytest
@@ -85,3 +88,14 @@ def test_mixed_exprb53_level8_12h_matches_fp64_path():
     area = G.cell_areas()
     m0, m1 = np.sum(area * u0[3 * G.ncells:]), np.sum(area * a[3 * G.ncells:])
     assert abs(m1 - m0) <= 1e-6 * m0
+
+
+def test_mixed_exprb53_level9_two_steps_match_fp64_path():
+    """Level 9 (2,621,442 cells): the FP32 kernel without staged indices."""
+    from paper_1805_02144_gb300.api import Grid
+    G = Grid(9)
+    u0 = balanced_state(G.cell_centres(), 3, 400.0)
+    a = _run(G, u0, "exprb53", 1800.0, 2, MIXED)
+    b = _run(G, u0, "exprb53", 1800.0, 2, {"tol": 1e-8})
+    eh, ev = rel_l2_parts(a, b, G.ncells)
+    assert eh <= 1e-5 and ev <= 1e-5, (eh, ev)
