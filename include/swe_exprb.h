@@ -277,7 +277,7 @@ int exprb_step_adjoint(swe_grid* grid, int scheme, double dt, const double* u_n,
  * stream around every persistent phi launch and every exprb_step / phi_action
  * call; counters of IOM2 iterations, w_j products and combination terms kept
  * on the device).  phi_flop is the operation count of the phi launches (per
- * cell: 342 per IOM2 iteration, 310 per w_j product, 8 per combination term;
+ * cell: 346 per IOM2 iteration, 310 per w_j product, 8 per combination term;
  * FP64 or FP32 by the launch's precision); phi_bytes the algorithmic vector
  * bytes (per cell with FP64 vectors: 136 per IOM2 iteration, 104 per w_j
  * product, 32 per combination term; half with FP32 vectors), operator tables
@@ -359,7 +359,7 @@ int swe_ensemble_stats(swe_ensemble* ens, phi_stats* stats, double* member_ms, i
 int swe_ensemble_shape(const swe_ensemble* ens, int* threads, int* blocks_per_sm, int* nblocks, int* ngroups,
                        int* member_group);
 /* Waits for `stream`; *flop = the algorithmic FP64 operation count of the
- * last run (per cell: 342 per IOM2 column, 310 per w_j product, 8 per
+ * last run (per cell: 346 per IOM2 column, 310 per w_j product, 8 per
  * substep-combination term, the counts swe_profile reports for phi_action),
  * summed over members. */
 int swe_ensemble_work(swe_ensemble* ens, double* flop, void* stream);

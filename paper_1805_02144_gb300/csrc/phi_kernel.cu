@@ -957,7 +957,7 @@ __device__ void phi_finish(const PhiArgsT<R>& a, Shared& sh) {
     if (S->status == SWE_OK) S->status = st;
     if (a.m_slot && st == SWE_OK && C->m_last > 0) *a.m_slot = C->m_last;
     if (a.prof) {
-      // per cell: IOM2 iteration 342 flop / 136 B, w_j product 310 / 104,
+      // per cell: IOM2 iteration 346 flop / 136 B, w_j product 310 / 104,
       // combination term 8 / 32 (bytes of FP64 vectors; FP32 vectors move half)
       const double cells = (double)ng, esz = (double)sizeof(R) / 8.0;
       a.prof->iters += C->n_iter;
