@@ -292,13 +292,18 @@ typedef struct {
   int64_t iom2_iterations, w_jv, comb_terms;
   /* time of the persistent launches by phase, as seen by block 0 (work plus
    * barrier wait): prologue, w_j pass 1, w_j pass 2, IOM2 pass 1, IOM2 pass 2
-   * (+ dots), orthogonalisation + next pass 1 (+ norm), controller tail and
+   * (+ its reduction: the window dots and the norm of the vector the previous
+   * orthogonalisation made), orthogonalisation + next pass 1 (+ a barrier, or
+   * the norm's own reduction after the last column), controller tail and
    * barrier, combination, Taylor exponential, controller head */
   double phase_ms[10];
   /* operator-table bytes the phi launches read (per cell, per IOM2 iteration
    * and per w_j product: 62 table reals and 12 int32 neighbour indices for a
    * pass 1 plus a pass 2), which a matrix-free stencil streams on top of the
-   * vector bytes */
+   * vector bytes.  A launch that keeps its neighbour indices in shared memory
+   * (the single-precision kernel when they fit) reads them once per launch
+   * but is counted the same way, so its figure includes 48 B per cell per
+   * iteration that it does not stream. */
   double phi_table_bytes;
 } swe_profile;
 
