@@ -1114,17 +1114,18 @@ struct PhiVariant {
   const void* fn;
   int threads;
 };
-static const PhiVariant kVariants[2][5] = {
-    {{(const void*)phi_kernel<double, 384, 1>, 384},
-     {(const void*)phi_kernel<double, 256, 2>, 256},
-     {(const void*)phi_kernel<double, 192, 2>, 192},
-     {(const void*)phi_kernel<double, 128, 3>, 128},
-     {(const void*)phi_kernel<double, 96, 4>, 96}},
-    {{(const void*)phi_kernel<float, 512, 2>, 512},
-     {(const void*)phi_kernel<float, 256, 3>, 256},
-     {(const void*)phi_kernel<float, 256, 2>, 256},
-     {(const void*)phi_kernel<float, 128, 3>, 128},
-     {(const void*)phi_kernel<float, 96, 4>, 96}},
+static const PhiVariant kVariantsF64[] = {
+    {(const void*)phi_kernel<double, 384, 1>, 384},
+    {(const void*)phi_kernel<double, 256, 2>, 256},
+    {(const void*)phi_kernel<double, 192, 2>, 192},
+    {(const void*)phi_kernel<double, 128, 3>, 128},
+    {(const void*)phi_kernel<double, 96, 4>, 96},
+};
+// One FP32 shape: two 512-thread blocks per SM hold the most threads at the
+// 64 registers the stencils fit in, which is how single-precision shapes are
+// ranked (below); smaller shapes never rank first and are not built.
+static const PhiVariant kVariantsF32[] = {
+    {(const void*)phi_kernel<float, 512, 2>, 512},
 };
 
 // Instantiations whose blocks keep their neighbour indices in shared memory,
@@ -1155,7 +1156,11 @@ int phi_select(int ng, int single, PhiLaunch* out) {
   if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -1;
   long long best = 0;
   bool found = false;
-  for (const PhiVariant& v : kVariants[single ? 1 : 0]) {
+  const PhiVariant* vs = single ? kVariantsF32 : kVariantsF64;
+  const int nv = single ? (int)(sizeof(kVariantsF32) / sizeof(kVariantsF32[0]))
+                        : (int)(sizeof(kVariantsF64) / sizeof(kVariantsF64[0]));
+  for (int q = 0; q < nv; ++q) {
+    const PhiVariant& v = vs[q];
     int per = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, v.fn, v.threads, 0) != cudaSuccess || per < 1)
       continue;
